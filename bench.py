@@ -1,0 +1,382 @@
+"""Benchmark of the bin-level q-gram filter on one (or N) GB300s.
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+  grim_build      pack the 3.1 Gbp reference, build the bin-major and the
+                  token-major bit-vector tables (15.5M bins, 1.98 GB each)
+  grim_filter     all-bins mode: every one of 1,000,000 reads (L=100, e=5)
+                  against every bin (tokenise, accumulate, threshold, compact)
+  grim_filter     candidate-list mode on the same reads (LogNormal lists,
+                  median 200, true bin included)
+``value`` is reads per second of that step with inputs resident in HBM;
+``e2e`` is the same through grim_build_host / grim_filter_host with pinned
+host buffers, the host<->device copies inside the timed region.
+
+``--impl reference`` times the CPU oracle (the only reference there is: the
+paper publishes no code) on a bounded sample of the same workload.
+
+Under torchrun each rank filters its own 1,000,000 reads against its own copy
+of the table (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "reads/s filtered vs whole 3.1 Gbp bin table"
+UNIT = "reads/s"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--genome", type=int, default=3_100_000_000, help="reference length (bases)")
+    p.add_argument("--reads", type=int, default=1_000_000, help="reads per rank")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args, rank: int):
+    from paper_1708_04329_gb300 import synth
+
+    t0 = time.perf_counter()
+    g = synth.human_genome(args.genome)
+    w = synth.human_exhaustive(n_reads=args.reads, g=g) if rank == 0 else None
+    if w is None:  # other ranks: their own reads (weak scaling)
+        rs = synth.reads(g, args.reads, seed=3 + 7919 * rank, lengths=(100,), e=5, max_edits=5)
+        w = dict(name="human_exhaustive", genome=g, B=200, q=5, max_read_len=100, reads=rs)
+    nb = (len(g) + w["B"] - 1) // w["B"]
+    off, cand = synth.candidates((w["reads"].true_pos // w["B"]).astype(np.int32), nb, seed=4 + rank)
+    w["cand_off"], w["cand"] = off, cand
+    w["gen_s"] = time.perf_counter() - t0
+    return w
+
+
+def config_of(args, w):
+    nb = (len(w["genome"]) + w["B"] - 1) // w["B"]
+    return {
+        "workload": (f"human-scale exhaustive: {len(w['genome']) / 1e9:.1f} Gbp synthetic genome "
+                     f"(41% GC, ~50% copies of 500 repeat families), B={w['B']}, q={w['q']}, "
+                     f"{nb} bins, {w['reads'].n} reads L=100 e=5 against every bin; step = "
+                     f"grim_build (both layouts) + all-bins grim_filter + candidate-list "
+                     f"grim_filter ({len(w['cand'])} candidates)"),
+        "genome_bases": len(w["genome"]), "bins": nb, "reads_per_gpu": w["reads"].n,
+        "candidates_per_gpu": int(len(w["cand"])), "B": w["B"], "q": w["q"], "e": 5,
+        "read_len": 100, "l2": "inputs larger than L2 (1.98 GB token-major table, 3.1 GB reference)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        self.f.flush()
+        rows = []
+        for line in Path(self.f.name).read_text().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if mx and s > 0.3 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max((num(r[3]) or 0) for r in rows)}
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+
+def run_native(args, rank, world, local):
+    import torch
+
+    from paper_1708_04329_gb300 import grim
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = workload(args, rank)
+    rs = w["reads"]
+    B, q, mrl = w["B"], w["q"], w["max_read_len"]
+    st = torch.cuda.current_stream()
+    dev = dict(
+        reads=torch.from_numpy(rs.seq).cuda(),
+        offsets=torch.from_numpy(rs.offsets.view(np.int64)).cuda(),
+        lens=torch.from_numpy(rs.lens.view(np.int32)).cuda(),
+        e=torch.from_numpy(rs.e.view(np.int16)).cuda())
+    cand = torch.from_numpy(w["cand"]).cuda()
+    cand_off = torch.from_numpy(w["cand_off"].view(np.int64)).cuda()
+    ref = torch.from_numpy(w["genome"]).cuda()
+    cap = 8 * rs.n + 4096
+    outs = [tuple(torch.empty(cap, dtype=dt, device="cuda") for dt in (torch.int32, torch.int32, torch.uint8))
+            for _ in range(2)]
+    ws = grim.Workspace()  # grows to the needed size on the first (warm-up) call
+
+    counts = {}
+
+    def step():
+        idx = grim.grim_build(ref, B, q, mrl, grim.GRIM_LAYOUT_BOTH, stream=st)
+        a = grim.grim_filter(idx, **dev, out=outs[0], workspace=ws, stream=st)
+        b = grim.grim_filter(idx, **dev, cand=cand, cand_off=cand_off, out=outs[1], workspace=ws,
+                             stream=st)
+        counts["all"], counts["cand"] = int(a[0].numel()), int(b[0].numel())
+        idx.close()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    grim.grim_profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    props = torch.cuda.get_device_properties(local)
+    uuid = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else str(uuid or local)
+    with ClockSampler(gpu_id) as clk:
+        torch.cuda.synchronize()
+        ev0.record(st)
+        for _ in range(args.steps):
+            step()
+        ev1.record(st)
+        torch.cuda.synchronize()
+    prof = grim.grim_profile_get()
+    grim.grim_profile(False)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+
+    # dominant kernel: the all-bins accumulate-and-threshold kernel
+    k_launch, k_ms = prof.get("exhaustive", (0, 0.0))
+    nb = (len(w["genome"]) + B - 1) // B
+    bit_tests = rs.n * nb * (100 - q + 1)  # algorithmic: L-q+1 tests per (read, bin)
+    per_launch_ms = k_ms / max(k_launch, 1)
+    peaks = {}
+    try:
+        peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    # shared-memory datapath: 128 B/clk/SM = 1024 bit tests/clk/SM
+    peak_tbit = n_sm * 1024 * sm_max * 1e6 / 1e12
+    achieved_tbit = bit_tests / (per_launch_ms / 1e3) / 1e12
+    traffic = None
+    roofline = {"bound": "alu", "achieved": round(achieved_tbit, 2), "peak": round(peak_tbit, 2),
+                "unit": "Tbit-tests/s", "frac": round(achieved_tbit / peak_tbit, 4),
+                "traffic": traffic,
+                "kernel": "k_exhaustive", "kernel_ms": round(per_launch_ms, 3),
+                "peak_basis": f"{n_sm} SMs x 128 B/clk shared-memory loads x 8 bits x {sm_max:.0f} MHz"}
+
+    stages = {k: round(v[1] / max(v[0], 1), 3) for k, v in prof.items()}
+    launches = int(sum(v[0] for v in prof.values()))
+    value = rs.n * world / (ms / args.steps / 1e3)
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic", "config": config_of(args, w),
+        "bin_checks_per_s": round(rs.n * nb * world / (ms / args.steps / 1e3), 1),
+        "filter_only_reads_per_s": round(rs.n / (per_launch_ms / 1e3), 1) if k_launch else None,
+        "passing_records": counts, "stage_ms_per_launch": stages,
+        "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = run_e2e(args, w, st)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, w, st):
+    """The same step through the host-buffer entry points, copies included."""
+    import torch
+
+    from paper_1708_04329_gb300 import grim
+
+    rs = w["reads"]
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t
+
+    h = dict(ref=pinned(w["genome"]), seq=pinned(rs.seq), off=pinned(rs.offsets.view(np.int64)),
+             lens=pinned(rs.lens.view(np.int32)), e=pinned(rs.e.view(np.int16)),
+             cand=pinned(w["cand"]), coff=pinned(w["cand_off"].view(np.int64)))
+    cap = 8 * rs.n + 4096
+    outs = [tuple(torch.empty(cap, dtype=dt).pin_memory() for dt in (torch.int32, torch.int32, torch.uint8))
+            for _ in range(2)]
+    nout = {}
+
+    def step():
+        idx = grim.grim_build_host(h["ref"], w["B"], w["q"], w["max_read_len"], stream=st)
+        a = grim.grim_filter_host(idx, h["seq"], h["off"], h["lens"], h["e"], out=outs[0], stream=st)
+        b = grim.grim_filter_host(idx, h["seq"], h["off"], h["lens"], h["e"], cand=h["cand"],
+                                  cand_off=h["coff"], out=outs[1], stream=st)
+        nout["a"], nout["b"] = len(a[0]), len(b[0])
+        idx.close()
+
+    step()  # warm the stream-ordered pool
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.e2e_steps
+    reads_bytes = rs.seq.nbytes + rs.offsets.nbytes + rs.lens.nbytes + rs.e.nbytes
+    h2d = w["genome"].nbytes + 2 * reads_bytes + w["cand"].nbytes + w["cand_off"].nbytes
+    d2h = 9 * (nout["a"] + nout["b"])
+    return {"value": round(rs.n / dt, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 3),
+            "steps": args.e2e_steps}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(w, budget_s: float) -> dict:
+    """The oracle as it stands on the host cores, on a bounded sample: the bit
+    vectors of every bin, then a few reads against every bin; reads/s is
+    extrapolated from the sample."""
+    import oracle
+
+    t0 = time.perf_counter()
+    oix = oracle.bin_vectors(w["genome"], w["B"], w["q"], w["max_read_len"])
+    build_s = time.perf_counter() - t0
+    rs = w["reads"]
+    n = oracle.threads()  # the oracle runs one read per thread
+    t_filter, done = 0.0, 0
+    while t_filter < budget_s and done < rs.n:
+        sub = rs.subset(range(done, min(done + n, rs.n)))
+        t1 = time.perf_counter()
+        oracle.filter(oix, sub)
+        t_filter += time.perf_counter() - t1
+        done += sub.n
+        n *= 2
+    return {"value": round(done / t_filter, 3), "unit": UNIT, "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": (f"reads 0..{done - 1} of the workload against all "
+                       f"{oix.num_bins} bins ({t_filter:.1f} s); the oracle's own bin-vector build "
+                       f"of the whole reference took {build_s:.1f} s and is not in the rate")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    w = workload(args, 0)
+    oix = oracle.bin_vectors(w["genome"], w["B"], w["q"], w["max_read_len"])
+    rs = w["reads"]
+    per_step = oracle.threads()  # one read per oracle thread
+    for s in range(args.warmup):
+        oracle.filter(oix, rs.subset(range(s * per_step, (s + 1) * per_step)))
+    t0 = time.perf_counter()
+    base = args.warmup * per_step
+    for s in range(args.steps):
+        oracle.filter(oix, rs.subset(range(base + s * per_step, base + (s + 1) * per_step)))
+    dt = (time.perf_counter() - t0) / args.steps
+    value = per_step / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": config_of(args, w),
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": oracle.threads(),
+                         "kind": "oracle",
+                         "sample": (f"each step: {per_step} reads of the workload against all "
+                                    f"{oix.num_bins} bins (the oracle's bin vectors built once "
+                                    f"before timing)")},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

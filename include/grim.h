@@ -1,0 +1,201 @@
+/*
+ * grim.h -- C-ABI of libgrim.so, a GB300 (sm_103a) implementation of the
+ * bin-level q-gram filter of GRIM-Filter (Kim et al., arXiv 1708.04329).
+ *
+ * The filter (§GRIM-Filter, Fig. 2, Fig. 3, Fig. 5):
+ *   - the reference of N bases is cut into bins of B bases; bin b's window is
+ *     [b*B, min(b*B + B + ext, N)) with ext = max_read_len - 1, so any read
+ *     whose first base lies in bin b's B-base core fits inside the window;
+ *   - each bin has a 4^q-bit vector: bit t is 1 iff token t (the base-4
+ *     number of q consecutive bases, A=0 C=1 G=2 T=3, first base most
+ *     significant, case folded) occurs wholly inside the window with no
+ *     other character in it;
+ *   - for a read of length L the L-q+1 tokens are extracted and, for each
+ *     candidate bin, their existence bits are summed (every position counts,
+ *     repeats included; a q-gram holding a non-ACGT character adds 0);
+ *   - the bin passes iff sum >= T = (L-q+1) - q*e (e = the read's edit
+ *     budget); T <= 0 makes every bin pass.
+ *
+ * Conventions for every call below:
+ *   - "device" pointers are CUDA device memory of the current device (for
+ *     example torch tensors' data_ptr()); "host" pointers are CPU memory
+ *     (page-locked memory gives the fastest copies);
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); work is
+ *     enqueued on it, and the calls that return results synchronise it;
+ *   - the caller owns every buffer it passes; the library keeps no caller
+ *     pointer after a call returns;
+ *   - errors are reported by the return value only (GRIM_OK = 0, negatives
+ *     below); nothing is thrown across the ABI and nothing aborts.
+ */
+#ifndef GRIM_H
+#define GRIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define GRIM_OK 0
+#define GRIM_E_ARG (-1)            /* bad argument (null pointer, bad size, bad CSR offsets)   */
+#define GRIM_E_NOMEM (-2)          /* device or host allocation failed                         */
+#define GRIM_E_CUDA (-3)           /* a CUDA call failed; grim_last_cuda_error() says which    */
+#define GRIM_E_READ_TOO_SHORT (-4) /* a read has L < q                                          */
+#define GRIM_E_READ_TOO_LONG (-5)  /* a read has L > max_read_len or L-q+1 > 255               */
+#define GRIM_E_BAD_CANDIDATE (-6)  /* a candidate bin is outside [0, num_bins)                  */
+#define GRIM_E_OVERFLOW (-7)       /* more passing records than `cap`; *n_out holds the total   */
+#define GRIM_E_TIMEOUT (-8)        /* a bounded device wait gave up                             */
+#define GRIM_E_WORKSPACE (-9)      /* workspace smaller than grim_filter_workspace_size()       */
+#define GRIM_E_NO_LAYOUT (-10)     /* the index lacks the table layout this call needs          */
+#define GRIM_E_UNSUPPORTED (-11)   /* parameter outside what this build implements              */
+
+/* ---- table layouts (bit mask for grim_build) ----------------------------- */
+/* Token-major: row t holds token t's bit for every bin, contiguous
+ * (§Mapping GRIM-Filter: one token's existence bits across all bins share a
+ * contiguous region, a bin's bits across tokens share a column).  Used by the
+ * all-bins filter. */
+#define GRIM_LAYOUT_TOKEN_MAJOR 1u
+/* Bin-major: bin b's 4^q-bit vector is contiguous (Fig. 2 column).  Used by
+ * the candidate-list filter. */
+#define GRIM_LAYOUT_BIN_MAJOR 2u
+
+typedef struct grim_index grim_index; /* opaque; owns its device tables */
+
+/* Description of a built index (all sizes in the units named). */
+typedef struct {
+  uint64_t ref_len;          /* N                                                   */
+  uint64_t num_bins;         /* ceil(N / B)                                         */
+  uint64_t num_bins_pad;     /* num_bins rounded up to a multiple of 1024           */
+  uint32_t B, q, ext;        /* bin core size, token length, extension (L_max - 1)  */
+  uint32_t max_read_len;     /* longest read the index accepts                      */
+  uint32_t layouts;          /* GRIM_LAYOUT_* bits present                          */
+  uint32_t words_per_bin;    /* uint32 words of one bin-major vector: max(1, 4^q/32) */
+  /* token-major table, device, uint32[4^q][num_bins_pad / 32]; bin b of row t
+   * is bit (b % 32) of word b / 32; padded bins are 0.  NULL if absent. */
+  const uint32_t* token_major;
+  /* bin-major table, device, uint32[num_bins][words_per_bin]; token t of bin
+   * b is bit (t % 32) of word t / 32.  NULL if absent. */
+  const uint32_t* bin_major;
+  uint64_t token_major_bytes, bin_major_bytes;
+} grim_index_desc;
+
+/*
+ * Build the bin bit vectors of a reference (§GRIM-Filter: the genome is
+ * scanned once, bit vectors are kept for reuse; Fig. 2).
+ *   ref           device, `len` ASCII bytes; A/C/G/T in either case are bases,
+ *                 any other byte is "not a base"
+ *   B             bin core size in bases, >= 1
+ *   q             token length, 2..6 (4^q bits per bin)
+ *   max_read_len  longest read to be filtered, >= q; ext = max_read_len - 1
+ *   layouts       nonzero mask of GRIM_LAYOUT_* to build
+ *   out           receives the index; free it with grim_free
+ * The index's tables are allocated by the library with cudaMalloc on the
+ * current device.  Synchronises `stream` before returning.
+ * Errors: GRIM_E_ARG, GRIM_E_UNSUPPORTED (q outside 2..6), GRIM_E_NOMEM,
+ * GRIM_E_CUDA.
+ */
+int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
+               uint32_t layouts, void* stream, grim_index** out);
+
+/* As grim_build, with `ref` in host memory; the copy to the device is part of
+ * the call. */
+int grim_build_host(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
+                    uint32_t layouts, void* stream, grim_index** out);
+
+/* Fill *out with the index's sizes and device table pointers. */
+int grim_index_info(const grim_index* idx, grim_index_desc* out);
+
+/* Release an index and its device tables (NULL is ignored). */
+void grim_free(grim_index* idx);
+
+/* Static description of a status code. */
+const char* grim_strerror(int status);
+
+/* The CUDA error string behind the last GRIM_E_CUDA of the calling thread. */
+const char* grim_last_cuda_error(void);
+
+/*
+ * Bytes of device workspace grim_filter needs for n_reads reads, n_cand
+ * candidates (0 in all-bins mode) and an output capacity of cap records.
+ */
+uint64_t grim_filter_workspace_size(const grim_index* idx, uint32_t n_reads, uint64_t n_cand,
+                                    uint64_t cap);
+
+/*
+ * Filter reads against the index (§GRIM-Filter steps 1-3: tokenise,
+ * accumulate existence bits, compare with the threshold of Fig. 3; the
+ * mapper's per-location check of Fig. 5 is the candidate-list mode).
+ *
+ *   reads      device, ASCII; read r is reads[offsets[r] .. offsets[r]+lens[r])
+ *   offsets    device, uint64[n_reads]
+ *   lens       device, uint32[n_reads]; every q <= lens[r] <= max_read_len
+ *   n_reads    number of reads (0 gives *n_out = 0)
+ *   e          device, uint16[n_reads], per-read absolute edit budget
+ *   cand       device, int32[n_cand] candidate bins, or NULL for every bin
+ *              (all-bins mode, needs the token-major layout)
+ *   cand_off   device, uint64[n_reads+1] CSR offsets into cand: read r's
+ *              candidates are cand[cand_off[r] .. cand_off[r+1]); must be
+ *              non-decreasing with cand_off[n_reads] == n_cand (candidate
+ *              mode needs the bin-major layout)
+ *   out_read, out_bin, out_count
+ *              device, uint32/uint32/uint8 [cap]: the passing records
+ *              (read, bin, sum), ordered by read, then by bin (all-bins
+ *              mode) or by position in the read's candidate list
+ *   cap        capacity of the three output arrays, in records
+ *   n_out      host; receives the number of passing records
+ *   workspace  device, >= grim_filter_workspace_size(idx, n_reads, n_cand, cap)
+ *              bytes, 256-byte aligned; contents need not be initialised
+ * Synchronises `stream` before returning.
+ * Errors: GRIM_E_ARG, GRIM_E_NO_LAYOUT, GRIM_E_WORKSPACE,
+ * GRIM_E_READ_TOO_SHORT, GRIM_E_READ_TOO_LONG, GRIM_E_BAD_CANDIDATE (these
+ * three in that order of precedence; output contents then unspecified),
+ * GRIM_E_OVERFLOW (*n_out = total passing records; outputs unspecified, call
+ * again with cap >= *n_out), GRIM_E_CUDA.
+ */
+int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offsets,
+                const uint32_t* lens, uint32_t n_reads, const uint16_t* e, const int32_t* cand,
+                const uint64_t* cand_off, uint64_t n_cand, uint32_t* out_read, uint32_t* out_bin,
+                uint8_t* out_count, uint64_t cap, uint64_t* n_out, void* workspace,
+                uint64_t workspace_bytes, void* stream);
+
+/*
+ * As grim_filter with every array in host memory.  The library allocates
+ * device staging (stream-ordered, returned to the pool before the call
+ * returns) and the host<->device copies are part of the call.
+ */
+int grim_filter_host(const grim_index* idx, const char* reads, const uint64_t* offsets,
+                     const uint32_t* lens, uint32_t n_reads, const uint16_t* e,
+                     const int32_t* cand, const uint64_t* cand_off, uint64_t n_cand,
+                     uint32_t* out_read, uint32_t* out_bin, uint8_t* out_count, uint64_t cap,
+                     uint64_t* n_out, void* stream);
+
+/* ---- helpers of the mapper around the filter (§GRIM-Filter, Fig. 5) ----- */
+
+/* Bin whose core holds reference position `loc`: loc / B. */
+uint64_t grim_loc_to_bin(const grim_index* idx, uint64_t loc);
+
+/* Edit budget for an error rate num/den of read length L, rounded up
+ * (Fig. 4 caption: the ceiling of read length times the error rate). */
+uint32_t grim_edits_for_rate(uint32_t L, uint32_t num, uint32_t den);
+
+/* ---- per-kernel timing -------------------------------------------------- */
+typedef struct {
+  char name[32];      /* kernel name                                 */
+  uint64_t launches;  /* launches timed since grim_profile(1)         */
+  double total_ms;    /* summed CUDA-event time on the launch stream  */
+} grim_kernel_time;
+
+/* Turn per-kernel CUDA-event timing on (1) or off (0); turning it on clears
+ * the counters.  Timing brackets each kernel launch with events recorded on
+ * the launch stream. */
+int grim_profile(int enable);
+
+/* Copy up to `max` per-kernel totals into out; returns how many there are. */
+int grim_profile_get(grim_kernel_time* out, int max);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRIM_H */

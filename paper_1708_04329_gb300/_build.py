@@ -87,7 +87,7 @@ def build_grim(force: bool = False, extra: list[str] | None = None) -> Path:
             list(ex.map(_run, jobs))
     if force or jobs or _stale(out, objs):
         tmp = out.with_suffix(f".so.tmp{os.getpid()}")
-        _run([nvcc] + ARCH + ["-shared", "-o", str(tmp)] + [str(o) for o in objs] + ["-lcudart"])
+        _run([nvcc] + ARCH + ["-shared", "--cudart", "static", "-o", str(tmp)] + [str(o) for o in objs])
         os.replace(tmp, out)
     return out
 

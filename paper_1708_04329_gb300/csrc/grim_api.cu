@@ -1,0 +1,449 @@
+// C-ABI of libgrim.so (include/grim.h): argument checks, index ownership,
+// workspace layout, the order of kernel launches, status reporting and the
+// optional per-kernel event timing.
+#include <mutex>
+#include <string.h>
+#include <string>
+#include <vector>
+
+#include "grim_internal.cuh"
+
+struct grim_index {
+  grim::IndexView v;
+  uint32_t layouts;
+  uint32_t* tm;
+  uint32_t* bm;
+};
+
+namespace grim {
+namespace {
+
+thread_local std::string g_cuda_err;
+
+int cuda_fail(cudaError_t e) {
+  g_cuda_err = cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? GRIM_E_NOMEM : GRIM_E_CUDA;
+}
+
+#define CK(call)                                 \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// token stride: the longest read's token count rounded up to a 16-token block
+inline uint32_t token_stride(const IndexView& v) {
+  const uint32_t nt = v.max_read_len - v.q + 1;
+  return (nt + kBlockTokens - 1) / kBlockTokens * kBlockTokens;
+}
+
+struct Layout {
+  uint64_t tok, meta, keys_a, keys_b, cnt_a, cnt_b, hist, total;
+};
+
+Layout layout(const IndexView& v, uint32_t n_reads, uint64_t cap) {
+  Layout L{};
+  uint64_t o = sizeof(Ctl);
+  L.tok = o;
+  o = align256(o + (uint64_t)n_reads * token_stride(v) * sizeof(uint16_t));
+  L.meta = o;
+  o = align256(o + (uint64_t)n_reads * sizeof(uint32_t));
+  L.keys_a = o;
+  o = align256(o + cap * sizeof(unsigned long long));
+  L.keys_b = o;
+  o = align256(o + cap * sizeof(unsigned long long));
+  L.cnt_a = o;
+  o = align256(o + cap);
+  L.cnt_b = o;
+  o = align256(o + cap);
+  L.hist = o;
+  o = align256(o + sort_workspace_bytes(cap));
+  L.total = o;
+  return L;
+}
+
+int status_to_code(uint32_t s) {
+  if (s & kStatusShort) return GRIM_E_READ_TOO_SHORT;
+  if (s & kStatusLong) return GRIM_E_READ_TOO_LONG;
+  if (s & kStatusBadCsr) return GRIM_E_ARG;
+  if (s & kStatusBadCand) return GRIM_E_BAD_CANDIDATE;
+  if (s & kStatusTimeout) return GRIM_E_TIMEOUT;
+  return GRIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-kernel timing
+// ---------------------------------------------------------------------------
+struct ProfEntry {
+  std::string name;
+  uint64_t launches = 0;
+  double ms = 0.0;
+};
+struct Pending {
+  int slot;
+  cudaEvent_t a, b;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfEntry> g_prof;
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event() {
+  if (!g_event_pool.empty()) {
+    cudaEvent_t e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+}  // namespace
+
+ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), st(s) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return;
+  int idx = -1;
+  for (size_t i = 0; i < g_prof.size(); ++i)
+    if (g_prof[i].name == name) idx = (int)i;
+  if (idx < 0) {
+    g_prof.push_back(ProfEntry{name});
+    idx = (int)g_prof.size() - 1;
+  }
+  Pending p{idx, take_event(), take_event()};
+  cudaEventRecord(p.a, st);
+  g_pending.push_back(p);
+  slot = (int)g_pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (slot < 0 || slot >= (int)g_pending.size()) return;
+  cudaEventRecord(g_pending[slot].b, st);
+}
+
+void prof_collect() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (const Pending& p : g_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess &&
+        p.slot < (int)g_prof.size()) {
+      g_prof[p.slot].launches += 1;
+      g_prof[p.slot].ms += ms;
+    }
+    g_event_pool.push_back(p.a);
+    g_event_pool.push_back(p.b);
+  }
+  g_pending.clear();
+}
+
+}  // namespace grim
+
+using namespace grim;
+
+extern "C" {
+
+const char* grim_strerror(int s) {
+  switch (s) {
+    case GRIM_OK: return "ok";
+    case GRIM_E_ARG: return "bad argument";
+    case GRIM_E_NOMEM: return "out of memory";
+    case GRIM_E_CUDA: return "CUDA error";
+    case GRIM_E_READ_TOO_SHORT: return "read shorter than q";
+    case GRIM_E_READ_TOO_LONG: return "read longer than max_read_len or more than 255 tokens";
+    case GRIM_E_BAD_CANDIDATE: return "candidate bin out of range";
+    case GRIM_E_OVERFLOW: return "more passing records than the output capacity";
+    case GRIM_E_TIMEOUT: return "bounded device wait gave up";
+    case GRIM_E_WORKSPACE: return "workspace too small";
+    case GRIM_E_NO_LAYOUT: return "index lacks the table layout this call needs";
+    case GRIM_E_UNSUPPORTED: return "parameter outside what this build implements";
+    default: return "unknown status";
+  }
+}
+
+const char* grim_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
+               uint32_t layouts, void* stream, grim_index** out) {
+  if (!out) return GRIM_E_ARG;
+  *out = nullptr;
+  if (!ref || len == 0 || B == 0 || max_read_len < q || layouts == 0 ||
+      (layouts & ~(GRIM_LAYOUT_TOKEN_MAJOR | GRIM_LAYOUT_BIN_MAJOR)))
+    return GRIM_E_ARG;
+  if (q < 2 || q > 6 || max_read_len - q + 1 > kMaxTokens) return GRIM_E_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  IndexView v{};
+  v.n = len;
+  v.B = B;
+  v.q = q;
+  v.ext = max_read_len - 1;
+  v.max_read_len = max_read_len;
+  v.r4 = 1u << (2 * q);
+  v.wpb = v.r4 >= 32 ? v.r4 / 32 : 1;
+  v.num_bins = (len + B - 1) / B;
+  v.num_bins_pad = (v.num_bins + kTileBins - 1) / kTileBins * kTileBins;
+  v.wpad = v.num_bins_pad / 32;
+  if (v.num_bins > 0xFFFFFFFFull) return GRIM_E_UNSUPPORTED;  // bins are uint32 in the output
+
+  grim_index* ix = new (std::nothrow) grim_index{};
+  if (!ix) return GRIM_E_NOMEM;
+  ix->layouts = layouts;
+  auto fail = [&](int code) {
+    cudaFree(ix->tm);
+    cudaFree(ix->bm);
+    delete ix;
+    return code;
+  };
+  cudaError_t e;
+  if (layouts & GRIM_LAYOUT_TOKEN_MAJOR) {
+    e = cudaMalloc(&ix->tm, (uint64_t)v.r4 * v.wpad * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+  }
+  if (layouts & GRIM_LAYOUT_BIN_MAJOR) {
+    e = cudaMalloc(&ix->bm, v.num_bins * v.wpb * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+  }
+  v.tm = ix->tm;
+  v.bm = ix->bm;
+  ix->v = v;
+
+  // packed reference (one spare word at the end of each array for the
+  // two-word reads of the token extraction)
+  const uint64_t n32 = (len + 31) / 32;
+  uint32_t *codes = nullptr, *invalid = nullptr;
+  e = cudaMallocAsync(&codes, (2 * n32 + 2) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  e = cudaMallocAsync(&invalid, (n32 + 2) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(codes, st);
+    return fail(cuda_fail(e));
+  }
+  cudaMemsetAsync(codes + 2 * n32, 0, 2 * sizeof(uint32_t), st);
+  cudaMemsetAsync(invalid + n32, 0xFF, 2 * sizeof(uint32_t), st);
+  launch_pack_ref(ref, len, codes, invalid, st);
+  if (ix->tm) launch_build_token_major(codes, invalid, v, ix->tm, st);
+  if (ix->bm) launch_build_bin_major(codes, invalid, v, ix->bm, st);
+  cudaFreeAsync(codes, st);
+  cudaFreeAsync(invalid, st);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  prof_collect();
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  *out = ix;
+  return GRIM_OK;
+}
+
+int grim_build_host(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
+                    uint32_t layouts, void* stream, grim_index** out) {
+  if (!out) return GRIM_E_ARG;
+  *out = nullptr;
+  if (!ref || len == 0) return GRIM_E_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* d = nullptr;
+  CK(cudaMallocAsync(&d, len, st));
+  cudaError_t e = cudaMemcpyAsync(d, ref, len, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(d, st);
+    return cuda_fail(e);
+  }
+  int rc = grim_build(d, len, B, q, max_read_len, layouts, stream, out);
+  cudaFreeAsync(d, st);
+  e = cudaStreamSynchronize(st);
+  if (rc == GRIM_OK && e != cudaSuccess) {
+    grim_free(*out);
+    *out = nullptr;
+    return cuda_fail(e);
+  }
+  return rc;
+}
+
+int grim_index_info(const grim_index* idx, grim_index_desc* out) {
+  if (!idx || !out) return GRIM_E_ARG;
+  const IndexView& v = idx->v;
+  memset(out, 0, sizeof(*out));
+  out->ref_len = v.n;
+  out->num_bins = v.num_bins;
+  out->num_bins_pad = v.num_bins_pad;
+  out->B = v.B;
+  out->q = v.q;
+  out->ext = v.ext;
+  out->max_read_len = v.max_read_len;
+  out->layouts = idx->layouts;
+  out->words_per_bin = v.wpb;
+  out->token_major = idx->tm;
+  out->bin_major = idx->bm;
+  out->token_major_bytes = idx->tm ? (uint64_t)v.r4 * v.wpad * sizeof(uint32_t) : 0;
+  out->bin_major_bytes = idx->bm ? v.num_bins * v.wpb * sizeof(uint32_t) : 0;
+  return GRIM_OK;
+}
+
+void grim_free(grim_index* idx) {
+  if (!idx) return;
+  cudaFree(idx->tm);
+  cudaFree(idx->bm);
+  delete idx;
+}
+
+uint64_t grim_filter_workspace_size(const grim_index* idx, uint32_t n_reads, uint64_t n_cand,
+                                    uint64_t cap) {
+  (void)n_cand;
+  if (!idx) return 0;
+  return layout(idx->v, n_reads, cap).total;
+}
+
+int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offsets,
+                const uint32_t* lens, uint32_t n_reads, const uint16_t* e, const int32_t* cand,
+                const uint64_t* cand_off, uint64_t n_cand, uint32_t* out_read, uint32_t* out_bin,
+                uint8_t* out_count, uint64_t cap, uint64_t* n_out, void* workspace,
+                uint64_t workspace_bytes, void* stream) {
+  if (!idx || !n_out) return GRIM_E_ARG;
+  *n_out = 0;
+  const bool cand_mode = cand != nullptr || cand_off != nullptr;
+  if (cand_mode && !cand_off) return GRIM_E_ARG;
+  if (cand_mode && n_cand && !cand) return GRIM_E_ARG;
+  if (cand_mode && !(idx->layouts & GRIM_LAYOUT_BIN_MAJOR)) return GRIM_E_NO_LAYOUT;
+  if (!cand_mode && !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR)) return GRIM_E_NO_LAYOUT;
+  if (!cand_mode && idx->v.q > 5) return GRIM_E_UNSUPPORTED;
+  if (n_reads == 0) return GRIM_OK;
+  if (!reads || !offsets || !lens || !e) return GRIM_E_ARG;
+  if (cap && (!out_read || !out_bin || !out_count)) return GRIM_E_ARG;
+  if (cap > 0xFFFFFFFFull) return GRIM_E_ARG;
+  const IndexView& v = idx->v;
+  const Layout L = layout(v, n_reads, cap);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return GRIM_E_ARG;
+  if (workspace_bytes < L.total) return GRIM_E_WORKSPACE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  Ctl* ctl = reinterpret_cast<Ctl*>(ws);
+  uint16_t* tokens = reinterpret_cast<uint16_t*>(ws + L.tok);
+  uint32_t* meta = reinterpret_cast<uint32_t*>(ws + L.meta);
+  RecordsView ra{reinterpret_cast<unsigned long long*>(ws + L.keys_a),
+                 reinterpret_cast<uint8_t*>(ws + L.cnt_a), cap};
+  RecordsView rb{reinterpret_cast<unsigned long long*>(ws + L.keys_b),
+                 reinterpret_cast<uint8_t*>(ws + L.cnt_b), cap};
+  ReadsView rv{tokens, meta, n_reads, token_stride(v)};
+  const uint32_t bin_bits = v.num_bins > 1 ? bit_length(v.num_bins - 1) : 0;
+
+  CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
+  launch_tokenise(reads, offsets, lens, e, v, rv, tokens, meta, ctl, st);
+  if (cand_mode) {
+    launch_check_candidates(cand, cand_off, n_reads, n_cand, v.num_bins, ctl, st);
+    launch_candidates(v, rv, cand, cand_off, ra, ctl, st);
+  } else {
+    launch_exhaustive(v, rv, ra, bin_bits, ctl, st);
+  }
+  CK(cudaGetLastError());
+  Ctl h{};
+  CK(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  prof_collect();
+  const int sc = status_to_code(h.status);
+  if (sc != GRIM_OK) return sc;
+  *n_out = h.n_rec;
+  if (h.n_rec > cap) return GRIM_E_OVERFLOW;
+  const uint32_t key_bits =
+      cand_mode ? bit_length(n_cand ? n_cand - 1 : 0)
+                : bin_bits + (n_reads > 1 ? bit_length((uint64_t)n_reads - 1) : 0);
+  sort_and_emit(ra, rb, h.n_rec, key_bits, ws + L.hist, cand_mode, bin_bits, cand, cand_off, n_reads,
+                out_read, out_bin, out_count, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  prof_collect();
+  return GRIM_OK;
+}
+
+int grim_filter_host(const grim_index* idx, const char* reads, const uint64_t* offsets,
+                     const uint32_t* lens, uint32_t n_reads, const uint16_t* e,
+                     const int32_t* cand, const uint64_t* cand_off, uint64_t n_cand,
+                     uint32_t* out_read, uint32_t* out_bin, uint8_t* out_count, uint64_t cap,
+                     uint64_t* n_out, void* stream) {
+  if (!idx || !n_out) return GRIM_E_ARG;
+  *n_out = 0;
+  const bool cand_mode = cand != nullptr || cand_off != nullptr;
+  if (n_reads == 0) return GRIM_OK;
+  if (!reads || !offsets || !lens || !e) return GRIM_E_ARG;
+  if (cand_mode && (!cand_off || (n_cand && !cand))) return GRIM_E_ARG;
+  if (cap && (!out_read || !out_bin || !out_count)) return GRIM_E_ARG;
+  uint64_t bytes = 0;
+  for (uint32_t r = 0; r < n_reads; ++r)
+    if (offsets[r] + lens[r] > bytes) bytes = offsets[r] + lens[r];
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t ws_bytes = grim_filter_workspace_size(idx, n_reads, n_cand, cap);
+  // one stream-ordered allocation holds every device copy
+  const uint64_t o_reads = 0;
+  const uint64_t o_off = align256(o_reads + (bytes ? bytes : 1));
+  const uint64_t o_lens = align256(o_off + (uint64_t)n_reads * 8);
+  const uint64_t o_e = align256(o_lens + (uint64_t)n_reads * 4);
+  const uint64_t o_cand = align256(o_e + (uint64_t)n_reads * 2);
+  const uint64_t o_coff = align256(o_cand + (cand_mode ? n_cand * 4 : 0));
+  const uint64_t o_or = align256(o_coff + (cand_mode ? ((uint64_t)n_reads + 1) * 8 : 0));
+  const uint64_t o_ob = align256(o_or + cap * 4);
+  const uint64_t o_oc = align256(o_ob + cap * 4);
+  const uint64_t o_ws = align256(o_oc + cap);
+  const uint64_t total = o_ws + ws_bytes;
+  char* d = nullptr;
+  CK(cudaMallocAsync(&d, total, st));
+  auto h2d = [&](uint64_t o, const void* src, uint64_t n) {
+    return n ? cudaMemcpyAsync(d + o, src, n, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  };
+  cudaError_t ce = h2d(o_reads, reads, bytes);
+  if (ce == cudaSuccess) ce = h2d(o_off, offsets, (uint64_t)n_reads * 8);
+  if (ce == cudaSuccess) ce = h2d(o_lens, lens, (uint64_t)n_reads * 4);
+  if (ce == cudaSuccess) ce = h2d(o_e, e, (uint64_t)n_reads * 2);
+  if (ce == cudaSuccess && cand_mode) ce = h2d(o_cand, cand, n_cand * 4);
+  if (ce == cudaSuccess && cand_mode) ce = h2d(o_coff, cand_off, ((uint64_t)n_reads + 1) * 8);
+  if (ce != cudaSuccess) {
+    cudaFreeAsync(d, st);
+    return cuda_fail(ce);
+  }
+  int rc = grim_filter(idx, d + o_reads, reinterpret_cast<const uint64_t*>(d + o_off),
+                       reinterpret_cast<const uint32_t*>(d + o_lens), n_reads,
+                       reinterpret_cast<const uint16_t*>(d + o_e),
+                       cand_mode ? reinterpret_cast<const int32_t*>(d + o_cand) : nullptr,
+                       cand_mode ? reinterpret_cast<const uint64_t*>(d + o_coff) : nullptr, n_cand,
+                       reinterpret_cast<uint32_t*>(d + o_or), reinterpret_cast<uint32_t*>(d + o_ob),
+                       reinterpret_cast<uint8_t*>(d + o_oc), cap, n_out, d + o_ws, ws_bytes, stream);
+  if (rc == GRIM_OK && *n_out) {
+    const uint64_t n = *n_out;
+    ce = cudaMemcpyAsync(out_read, d + o_or, n * 4, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out_bin, d + o_ob, n * 4, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out_count, d + o_oc, n, cudaMemcpyDeviceToHost, st);
+    if (ce != cudaSuccess) rc = cuda_fail(ce);
+  }
+  cudaFreeAsync(d, st);
+  ce = cudaStreamSynchronize(st);
+  if (rc == GRIM_OK && ce != cudaSuccess) rc = cuda_fail(ce);
+  return rc;
+}
+
+uint64_t grim_loc_to_bin(const grim_index* idx, uint64_t loc) { return idx ? loc / idx->v.B : 0; }
+
+uint32_t grim_edits_for_rate(uint32_t L, uint32_t num, uint32_t den) {
+  if (den == 0) return 0;
+  return (uint32_t)(((uint64_t)L * num + den - 1) / den);
+}
+
+int grim_profile(int enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof_on = enable != 0;
+  if (g_prof_on) g_prof.clear();
+  return GRIM_OK;
+}
+
+int grim_profile_get(grim_kernel_time* out, int max) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  const int n = (int)g_prof.size();
+  for (int i = 0; i < n && i < max && out; ++i) {
+    memset(&out[i], 0, sizeof(out[i]));
+    strncpy(out[i].name, g_prof[i].name.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = g_prof[i].launches;
+    out[i].total_ms = g_prof[i].ms;
+  }
+  return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Index build (§GRIM-Filter: the reference is scanned once and every bin's
+// bit vector is set from the tokens that occur in it; Fig. 2):
+//   k_pack_ref          ASCII -> 2-bit codes + not-a-base mask
+//   k_build_bin_major   one warp per bin, bit vector in shared memory
+//   k_build_token_major one CTA per 1024-bin tile (256 bins at q = 6), the
+//                       tile's [4^q rows x tile words] bitmap in shared memory
+// Both table builders scan the packed reference directly; neither is a
+// transpose of the other.
+#include "grim_internal.cuh"
+
+namespace grim {
+namespace {
+
+// A/C/G/T (either case) -> 0/1/2/3; `ok` false for any other byte.
+// Clearing bit 5 folds lowercase letters only ('a' 0x61 -> 'A' 0x41); the
+// 2-bit code of the folded letter is ((u >> 1) ^ (u >> 2)) & 3 for exactly
+// A (0x41), C (0x43), G (0x47) and T (0x54).
+__device__ __forceinline__ uint32_t base_code(uint32_t c, bool& ok) {
+  uint32_t u = c & 0xDFu;
+  ok = (u == 0x41u) | (u == 0x43u) | (u == 0x47u) | (u == 0x54u);
+  return ((u >> 1) ^ (u >> 2)) & 3u;
+}
+
+// Thread t packs bases [32t, 32t+32): two code words and one mask word.
+__global__ void k_pack_ref(const char* __restrict__ ref, uint64_t n, uint32_t* __restrict__ codes,
+                           uint32_t* __restrict__ invalid, uint64_t n32) {
+  uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (t >= n32) return;
+  uint64_t base = t * 32;
+  uint8_t b[32];
+  if (base + 32 <= n && ((reinterpret_cast<uintptr_t>(ref) & 15u) == 0)) {
+    const uint4* p = reinterpret_cast<const uint4*>(ref + base);
+    uint4 v0 = __ldg(p), v1 = __ldg(p + 1);
+    uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+    for (int i = 0; i < 32; ++i) b[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) b[i] = (base + i < n) ? (uint8_t)ref[base + i] : (uint8_t)'N';
+  }
+  uint32_t c0 = 0, c1 = 0, inv = 0;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    bool ok;
+    uint32_t c = base_code(b[i], ok);
+    if (!ok) { inv |= 1u << i; c = 0; }
+    if (i < 16) c0 |= c << (30 - 2 * i);
+    else c1 |= c << (30 - 2 * (i - 16));
+  }
+  codes[2 * t] = c0;
+  codes[2 * t + 1] = c1;
+  invalid[t] = inv;
+}
+
+// Token starting at reference position p, or -1 if one of its q bases is not
+// a base.  Needs p + q <= n (the packed arrays carry one spare word).
+__device__ __forceinline__ int32_t token_at(const uint32_t* __restrict__ codes,
+                                            const uint32_t* __restrict__ invalid, uint64_t p,
+                                            uint32_t q) {
+  uint64_t k = p >> 4;
+  uint64_t w = ((uint64_t)__ldg(codes + k) << 32) | __ldg(codes + k + 1);
+  uint32_t tok = (uint32_t)((w << (2 * (p & 15))) >> (64 - 2 * q));
+  uint64_t m = p >> 5;
+  uint64_t iw = (uint64_t)__ldg(invalid + m) | ((uint64_t)__ldg(invalid + m + 1) << 32);
+  uint32_t bad = (uint32_t)(iw >> (p & 31)) & ((1u << q) - 1u);
+  return bad ? -1 : (int32_t)tok;
+}
+
+// One warp per bin: set bit t of the bin's vector for every token wholly
+// inside window [bB, min(bB+B+ext, n)).
+__global__ void k_build_bin_major(const uint32_t* __restrict__ codes,
+                                  const uint32_t* __restrict__ invalid, IndexView ix,
+                                  uint32_t* __restrict__ bm) {
+  extern __shared__ uint32_t s_vec[];  // [warps][wpb]
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t b = blockIdx.x * (uint64_t)(blockDim.x >> 5) + warp;
+  uint32_t* v = s_vec + warp * ix.wpb;
+  for (uint32_t i = lane; i < ix.wpb; i += 32) v[i] = 0;
+  __syncwarp();
+  if (b < ix.num_bins) {
+    uint64_t lo = b * ix.B;
+    uint64_t hi = lo + ix.B + ix.ext;
+    if (hi > ix.n) hi = ix.n;
+    for (uint64_t p = lo + lane; p + ix.q <= hi; p += 32) {
+      int32_t t = token_at(codes, invalid, p, ix.q);
+      if (t >= 0) atomicOr(v + (t >> 5), 1u << (t & 31));
+    }
+  }
+  __syncwarp();
+  if (b < ix.num_bins)
+    for (uint32_t i = lane; i < ix.wpb; i += 32) bm[b * ix.wpb + i] = v[i];
+}
+
+// One CTA per tile of tile_words*32 bins: every q-gram start p that lies in a
+// window of the tile's bins sets its token's bit in each bin b whose window
+// holds it, i.e. b*B <= p and p+q <= b*B+B+ext.
+__global__ void __launch_bounds__(512) k_build_token_major(const uint32_t* __restrict__ codes,
+                                                           const uint32_t* __restrict__ invalid,
+                                                           IndexView ix, uint32_t tile_words,
+                                                           uint32_t* __restrict__ tm) {
+  extern __shared__ uint32_t s_tile[];  // [r4][tile_words]
+  const uint32_t nwords = ix.r4 * tile_words;
+  for (uint32_t i = threadIdx.x; i < nwords; i += blockDim.x) s_tile[i] = 0;
+  __syncthreads();
+  const uint64_t b0 = (uint64_t)blockIdx.x * tile_words * 32;
+  uint64_t b1 = b0 + (uint64_t)tile_words * 32;
+  if (b1 > ix.num_bins) b1 = ix.num_bins;
+  if (b0 < b1) {
+    const uint64_t p_lo = b0 * ix.B;
+    // last start: p + q <= min(n, (b1-1)*B + B + ext)
+    uint64_t end = b1 * ix.B + ix.ext;
+    if (end > ix.n) end = ix.n;
+    for (uint64_t p = p_lo + threadIdx.x; p + ix.q <= end; p += blockDim.x) {
+      int32_t t = token_at(codes, invalid, p, ix.q);
+      if (t < 0) continue;
+      const uint64_t x = p + ix.q;
+      uint64_t lo = x >= (uint64_t)ix.ext + 1 ? (x - ix.ext - 1) / ix.B : 0;
+      uint64_t hi = p / ix.B;
+      if (lo < b0) lo = b0;
+      if (hi > b1 - 1) hi = b1 - 1;
+      for (uint64_t b = lo; b <= hi; ++b) {
+        uint32_t rel = (uint32_t)(b - b0);
+        atomicOr(s_tile + (uint32_t)t * tile_words + (rel >> 5), 1u << (rel & 31));
+      }
+    }
+  }
+  __syncthreads();
+  const uint64_t w0 = (uint64_t)blockIdx.x * tile_words;
+  for (uint32_t i = threadIdx.x; i < nwords; i += blockDim.x) {
+    uint32_t t = i / tile_words, w = i % tile_words;
+    tm[(uint64_t)t * ix.wpad + w0 + w] = s_tile[i];
+  }
+}
+
+}  // namespace
+
+void launch_pack_ref(const char* ref, uint64_t n, uint32_t* codes, uint32_t* invalid,
+                     cudaStream_t st) {
+  uint64_t n32 = (n + 31) / 32;
+  if (n32 == 0) return;
+  ProfScope ps("pack_ref", st);
+  k_pack_ref<<<(unsigned)((n32 + 255) / 256), 256, 0, st>>>(ref, n, codes, invalid, n32);
+}
+
+void launch_build_bin_major(const uint32_t* codes, const uint32_t* invalid, const IndexView& ix,
+                            uint32_t* bm, cudaStream_t st) {
+  if (ix.num_bins == 0) return;
+  const uint32_t warps = 8;
+  uint64_t grid = (ix.num_bins + warps - 1) / warps;
+  ProfScope ps("build_bin_major", st);
+  k_build_bin_major<<<(unsigned)grid, warps * 32, warps * ix.wpb * sizeof(uint32_t), st>>>(
+      codes, invalid, ix, bm);
+}
+
+void launch_build_token_major(const uint32_t* codes, const uint32_t* invalid, const IndexView& ix,
+                              uint32_t* tm, cudaStream_t st) {
+  if (ix.num_bins == 0) return;
+  // 128 KB of shared memory per tile: 32 words (1024 bins) up to q = 5,
+  // 8 words (256 bins) at q = 6
+  uint32_t tile_words = ix.r4 <= 1024 ? 32u : 32768u / ix.r4;
+  size_t smem = (size_t)ix.r4 * tile_words * sizeof(uint32_t);
+  cudaFuncSetAttribute(k_build_token_major, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  uint64_t grid = (ix.num_bins_pad / 32) / tile_words;
+  ProfScope ps("build_token_major", st);
+  k_build_token_major<<<(unsigned)grid, 512, smem, st>>>(codes, invalid, ix, tile_words, tm);
+}
+
+}  // namespace grim

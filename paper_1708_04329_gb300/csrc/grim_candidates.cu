@@ -1,0 +1,191 @@
+// Candidate-list filter over the bin-major table (§GRIM-Filter: for each
+// candidate location the mapper asks whether the bin holding it can possibly
+// match; steps 2-3 and Fig. 5).
+//
+// GB300 mapping
+// -------------
+// * One warp per read (taken from a global counter).  The read's tokens are
+//   turned into a multiplicity histogram (a byte per token value) and then
+//   into bit planes P_k = {t : bit k of mult(t) is 1}, held in registers, so
+//   that for any bin vector v the token sum is
+//       sum = sum_k 2^k * popcount(v & P_k)
+//   -- every position counts, repeats included, with a handful of AND +
+//   POPC per 32 bits instead of one bit test per token.
+// * A bin vector (4^q bits) is gathered by G lanes with 16-byte loads
+//   (q = 5: 8 lanes x 16 B = 128 B, four candidates per warp step; q = 6:
+//   32 lanes x 16 B = 512 B); the lane group reduces its partial sums with
+//   shuffles and compares with T = (L-q+1) - q*e.
+// * The path is a random 128/512-byte gather per (read, bin) pair: bound by
+//   HBM, not by arithmetic.
+#include "grim_internal.cuh"
+
+namespace grim {
+namespace {
+
+template <int WPB>
+struct Cfg {
+  static constexpr int WL = WPB >= 4 ? 4 : WPB;  // words per lane
+  static constexpr int G = WPB / WL;             // lanes per candidate
+  static constexpr int CPW = 32 / G;             // candidates per warp step
+};
+
+template <int WL>
+__device__ __forceinline__ void load_words(const uint32_t* p, uint32_t (&v)[WL]) {
+  if constexpr (WL == 4) {
+    const uint4 x = __ldg(reinterpret_cast<const uint4*>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+  } else if constexpr (WL == 2) {
+    const uint2 x = __ldg(reinterpret_cast<const uint2*>(p));
+    v[0] = x.x; v[1] = x.y;
+  } else {
+    v[0] = __ldg(p);
+  }
+}
+
+struct CandArgs {
+  IndexView ix;
+  ReadsView rv;
+  const int32_t* cand;
+  const uint64_t* cand_off;
+  RecordsView rec;
+  Ctl* ctl;
+};
+
+constexpr int kWarps = 8;
+
+template <int WPB>
+__global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
+  using C = Cfg<WPB>;
+  constexpr int WL = C::WL, G = C::G, CPW = C::CPW;
+  extern __shared__ uint32_t s_hist[];  // [warps][hist_words]: byte t = multiplicity of token t
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t r4 = a.ix.r4;
+  const uint32_t hist_words = r4 >= 4 ? r4 / 4 : 1;
+  uint32_t* hist = s_hist + warp * hist_words;
+  const uint32_t sub = lane % G;     // this lane's slice of a bin vector
+  const uint32_t slot = lane / G;    // which of the warp's CPW candidates
+  if (*(volatile uint32_t*)&a.ctl->status) return;
+
+  for (;;) {
+    uint32_t r = 0;
+    if (lane == 0) r = atomicAdd(&a.ctl->item, 1u);
+    r = __shfl_sync(0xFFFFFFFFu, r, 0);
+    if (r >= a.rv.n_reads) break;
+    const uint64_t c0 = a.cand_off[r], c1 = a.cand_off[r + 1];
+    if (c0 == c1) continue;
+
+    // multiplicity histogram of the read's clean tokens
+    for (uint32_t i = lane; i < hist_words; i += 32) hist[i] = 0;
+    __syncwarp();
+    const uint32_t m = a.rv.meta[r];
+    const uint32_t ntok = m & 0xFFu, dmax = (m >> 8) & 0xFFu;
+    const uint16_t* tk = a.rv.tokens + (uint64_t)r * a.rv.ts;
+    for (uint32_t j = lane; j < ntok; j += 32) {
+      const uint32_t t = tk[j];
+      if (t < r4) atomicAdd(hist + (t >> 2), 1u << (8 * (t & 3u)));
+    }
+    __syncwarp();
+
+    // bit planes of the multiplicities for this lane's WL words
+    uint32_t P[8][WL];
+    uint32_t mx = 0;
+#pragma unroll
+    for (int w = 0; w < WL; ++w) {
+      const uint32_t wi = sub * WL + w;  // word index in the vector: tokens wi*32 .. wi*32+31
+      uint32_t hw[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t h = wi * 8 + j;
+        hw[j] = h < hist_words && (wi * 32 + 4 * j) < r4 ? hist[h] : 0u;
+        mx = max(mx, max(max(hw[j] & 0xFFu, (hw[j] >> 8) & 0xFFu),
+                         max((hw[j] >> 16) & 0xFFu, hw[j] >> 24)));
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        uint32_t pw = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          uint32_t x = (hw[j] >> k) & 0x01010101u;  // bit k of 4 byte counters
+          x |= x >> 7;
+          x |= x >> 14;
+          pw |= (x & 0xFu) << (4 * j);
+        }
+        P[k][w] = pw;
+      }
+    }
+    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+    const uint32_t K = 32 - __clz(mx);  // planes in use
+    const uint32_t thr = ntok - dmax;   // pass iff sum >= (L-q+1) - min(q*e, L-q+1)
+
+    for (uint64_t kb = c0; kb < c1; kb += CPW) {
+      const uint64_t k = kb + slot;
+      const bool valid = k < c1;
+      uint32_t sum = 0;
+      if (valid) {
+        const uint32_t b = (uint32_t)__ldg(a.cand + k);
+        uint32_t v[WL];
+        load_words<WL>(a.ix.bm + (uint64_t)b * WPB + sub * WL, v);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          if ((uint32_t)p < K) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < WL; ++w) s += __popc(v[w] & P[p][w]);
+            sum += s << p;
+          }
+        }
+      }
+#pragma unroll
+      for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+      const bool pass = valid && sub == 0 && sum >= thr;
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
+      if (bal) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)__popc(bal));
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (pass) {
+          const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+          if (pos < a.rec.cap) {
+            a.rec.keys[pos] = k;
+            a.rec.counts[pos] = (uint8_t)sum;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int WPB>
+void launch_t(const CandArgs& a, cudaStream_t st) {
+  const uint32_t hist_words = a.ix.r4 >= 4 ? a.ix.r4 / 4 : 1;
+  const size_t smem = (size_t)kWarps * hist_words * sizeof(uint32_t);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_candidates<WPB>, kWarps * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  uint64_t want = ((uint64_t)a.rv.n_reads + kWarps - 1) / kWarps;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (grid > want) grid = want;
+  if (grid < 1) grid = 1;
+  ProfScope ps("candidates", st);
+  k_candidates<WPB><<<(unsigned)grid, kWarps * 32, smem, st>>>(a);
+}
+
+}  // namespace
+
+void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
+                       const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st) {
+  if (rv.n_reads == 0) return;
+  CandArgs a{ix, rv, cand, cand_off, rec, ctl};
+  switch (ix.wpb) {
+    case 1: launch_t<1>(a, st); break;
+    case 2: launch_t<2>(a, st); break;
+    case 8: launch_t<8>(a, st); break;
+    case 32: launch_t<32>(a, st); break;
+    case 128: launch_t<128>(a, st); break;
+    default: break;  // q outside 2..6 is rejected by grim_build
+  }
+}
+
+}  // namespace grim

@@ -1,0 +1,169 @@
+// Stream compaction of the passing (read, bin, count) records
+// (§Mapping GRIM-Filter: the filter's result per read is a vector over bins;
+// here only the set entries are kept, read by read).
+//
+// The filter kernels append records in whatever order their warps finish, so
+// the order is restored by a least-significant-digit radix sort on the record
+// key -- (read << bin_bits | bin) in all-bins mode, the global candidate index
+// in candidate mode; keys are unique, so the output order is unique too.
+// Each 8-bit pass is a per-block digit histogram, one exclusive scan over
+// all blocks' histograms, and a stable scatter (per-warp ranks from
+// __match_any_sync, then warp order, then round order).  A last kernel splits
+// the keys into the caller's read / bin / count arrays.
+#include "grim_internal.cuh"
+
+namespace grim {
+namespace {
+
+constexpr uint32_t kSortThreads = 256;
+constexpr uint32_t kSortItems = 16;  // per thread per pass
+constexpr uint32_t kSortTile = kSortThreads * kSortItems;
+
+__global__ void __launch_bounds__(kSortThreads) k_rs_hist(const unsigned long long* __restrict__ keys,
+                                                          uint64_t n, uint32_t shift,
+                                                          uint32_t* __restrict__ hist, uint32_t nb) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+  for (uint32_t i = 0; i < kSortItems; ++i) {
+    const uint64_t idx = base + (uint64_t)i * kSortThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  hist[(uint64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Exclusive scan of m counters with one block: thread t owns a contiguous
+// segment, scans its sums across the block, then rewrites its segment.
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ h, uint64_t m) {
+  __shared__ uint32_t part[1024];
+  const uint64_t per = (m + 1023) / 1024;
+  const uint64_t lo = threadIdx.x * per;
+  const uint64_t hi = lo + per < m ? lo + per : m;
+  uint32_t s = 0;
+  for (uint64_t i = lo; i < hi; ++i) s += h[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (uint32_t d = 1; d < 1024; d <<= 1) {
+    const uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[threadIdx.x] - s;
+  for (uint64_t i = lo; i < hi; ++i) {
+    const uint32_t v = h[i];
+    h[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
+    const unsigned long long* __restrict__ kin, const uint8_t* __restrict__ cin,
+    unsigned long long* __restrict__ kout, uint8_t* __restrict__ cout, uint64_t n, uint32_t shift,
+    const uint32_t* __restrict__ hist, uint32_t nb) {
+  constexpr uint32_t kW = kSortThreads / 32;
+  __shared__ uint32_t s_base[256];
+  __shared__ uint32_t s_wcnt[kW][256];
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  s_base[tid] = hist[(uint64_t)tid * nb + blockIdx.x];
+  const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
+  for (uint32_t round = 0; round < kSortItems; ++round) {
+    for (uint32_t i = tid; i < kW * 256; i += kSortThreads) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const uint64_t idx = base + (uint64_t)round * kSortThreads + tid;
+    const bool valid = idx < n;
+    unsigned long long key = valid ? kin[idx] : 0ull;
+    const uint8_t c = valid ? cin[idx] : (uint8_t)0;
+    const uint32_t d = (uint32_t)(key >> shift) & 0xFFu;
+    // invalid lanes get a value no valid digit has, so they never match
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, valid ? d : 256u + lane);
+    const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) s_wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t off = s_base[d] + rank;
+      for (uint32_t w = 0; w < warp; ++w) off += s_wcnt[w][d];
+      kout[off] = key;
+      cout[off] = c;
+    }
+    __syncthreads();
+    uint32_t add = 0;
+    for (uint32_t w = 0; w < kW; ++w) add += s_wcnt[w][tid];
+    s_base[tid] += add;
+    __syncthreads();  // s_wcnt is cleared again at the top of the next round
+  }
+}
+
+__global__ void k_emit(const unsigned long long* __restrict__ keys,
+                       const uint8_t* __restrict__ counts, uint64_t n, bool cand_mode,
+                       uint32_t bin_bits, const int32_t* __restrict__ cand,
+                       const uint64_t* __restrict__ cand_off, uint32_t n_reads,
+                       uint32_t* __restrict__ out_read, uint32_t* __restrict__ out_bin,
+                       uint8_t* __restrict__ out_count) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long key = keys[i];
+  uint32_t r, b;
+  if (cand_mode) {
+    b = (uint32_t)cand[key];
+    // largest r with cand_off[r] <= key
+    uint32_t lo = 0, hi = n_reads - 1;
+    while (lo < hi) {
+      const uint32_t mid = lo + (hi - lo + 1) / 2;
+      if (cand_off[mid] <= key) lo = mid;
+      else hi = mid - 1;
+    }
+    r = lo;
+  } else {
+    r = (uint32_t)(key >> bin_bits);
+    b = (uint32_t)(key & ((bin_bits >= 64) ? ~0ull : ((1ull << bin_bits) - 1ull)));
+  }
+  out_read[i] = r;
+  out_bin[i] = b;
+  out_count[i] = counts[i];
+}
+
+}  // namespace
+
+uint64_t sort_workspace_bytes(uint64_t cap) {
+  const uint64_t nb = (cap + kSortTile - 1) / kSortTile;
+  return 256ull * (nb ? nb : 1) * sizeof(uint32_t);
+}
+
+void sort_and_emit(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
+                   bool candidate_mode, uint32_t bin_bits, const int32_t* cand,
+                   const uint64_t* cand_off, uint32_t n_reads, uint32_t* out_read,
+                   uint32_t* out_bin, uint8_t* out_count, cudaStream_t st) {
+  if (n == 0) return;
+  const uint32_t nb = (uint32_t)((n + kSortTile - 1) / kSortTile);
+  uint32_t* h = static_cast<uint32_t*>(hist);
+  RecordsView src = a, dst = b;
+  const uint32_t passes = (key_bits + 7) / 8;
+  for (uint32_t p = 0; p < passes; ++p) {
+    const uint32_t shift = 8 * p;
+    {
+      ProfScope ps("sort_hist", st);
+      k_rs_hist<<<nb, kSortThreads, 0, st>>>(src.keys, n, shift, h, nb);
+    }
+    {
+      ProfScope ps("sort_scan", st);
+      k_rs_scan<<<1, 1024, 0, st>>>(h, 256ull * nb);
+    }
+    {
+      ProfScope ps("sort_scatter", st);
+      k_rs_scatter<<<nb, kSortThreads, 0, st>>>(src.keys, src.counts, dst.keys, dst.counts, n,
+                                                shift, h, nb);
+    }
+    RecordsView t = src;
+    src = dst;
+    dst = t;
+  }
+  ProfScope ps("emit", st);
+  k_emit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src.keys, src.counts, n, candidate_mode,
+                                                      bin_bits, cand, cand_off, n_reads, out_read,
+                                                      out_bin, out_count);
+}
+
+}  // namespace grim

@@ -1,0 +1,92 @@
+// Read tokenising (§GRIM-Filter step 1: every token of the read is
+// extracted) and the per-read threshold of Fig. 3, plus the validation of
+// candidate lists.
+#include "grim_internal.cuh"
+
+namespace grim {
+namespace {
+
+// One warp per read.  tokens[r*ts + j] is the table row of token j:
+// its value for a clean q-gram, rowInvalid for one holding a non-base (it
+// still counts among the L-q+1 tokens and can never be found), rowPad past
+// the last token.  meta[r] = ntok | D' << 8 with D' = min(q*e, ntok): a bin
+// passes iff at most D' of the read's tokens are missing from it, which is
+// sum >= (L-q+1) - q*e.
+__global__ void k_tokenise(const char* __restrict__ reads, const uint64_t* __restrict__ offsets,
+                           const uint32_t* __restrict__ lens, const uint16_t* __restrict__ e,
+                           uint32_t n_reads, uint32_t q, uint32_t max_read_len, uint32_t r4,
+                           uint32_t ts, uint16_t* __restrict__ tokens, uint32_t* __restrict__ meta,
+                           Ctl* ctl) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  if (r >= n_reads) return;
+  const uint32_t L = lens[r];
+  const uint64_t off = offsets[r];
+  uint16_t* out = tokens + r * ts;
+  bool bad = false;
+  if (L < q) {
+    if (lane == 0) atomicOr(&ctl->status, kStatusShort);
+    bad = true;
+  } else if (L > max_read_len || L - q + 1 > kMaxTokens) {
+    if (lane == 0) atomicOr(&ctl->status, kStatusLong);
+    bad = true;
+  }
+  const uint32_t ntok = bad ? 0 : L - q + 1;
+  for (uint32_t j = lane; j < ts; j += 32) {
+    uint32_t row = rowPad(r4);
+    if (j < ntok) {
+      uint32_t v = 0;
+      bool clean = true;
+      for (uint32_t i = 0; i < q; ++i) {
+        uint32_t u = (uint8_t)reads[off + j + i] & 0xDFu;  // fold lowercase letters
+        clean &= (u == 0x41u) | (u == 0x43u) | (u == 0x47u) | (u == 0x54u);
+        v = (v << 2) | (((u >> 1) ^ (u >> 2)) & 3u);  // A0 C1 G2 T3
+      }
+      row = clean ? v : rowInvalid(r4);
+    }
+    out[j] = (uint16_t)row;
+  }
+  if (lane == 0) {
+    uint32_t d = q * (uint32_t)e[r];
+    if (d > ntok) d = ntok;
+    meta[r] = ntok | (d << 8);
+  }
+}
+
+__global__ void k_check_candidates(const int32_t* __restrict__ cand,
+                                   const uint64_t* __restrict__ cand_off, uint32_t n_reads,
+                                   uint64_t n_cand, uint64_t num_bins, Ctl* ctl) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < n_cand) {
+    int32_t b = cand[i];
+    if (b < 0 || (uint64_t)b >= num_bins) atomicOr(&ctl->status, kStatusBadCand);
+  }
+  if (i < n_reads) {
+    if (cand_off[i] > cand_off[i + 1]) atomicOr(&ctl->status, kStatusBadCsr);
+  }
+  if (i == 0 && cand_off[n_reads] != n_cand) atomicOr(&ctl->status, kStatusBadCsr);
+}
+
+}  // namespace
+
+void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t* lens,
+                     const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
+                     uint32_t* meta, Ctl* ctl, cudaStream_t st) {
+  if (rv.n_reads == 0) return;
+  const uint32_t threads = 256;
+  uint64_t grid = ((uint64_t)rv.n_reads * 32 + threads - 1) / threads;
+  ProfScope ps("tokenise", st);
+  k_tokenise<<<(unsigned)grid, threads, 0, st>>>(reads, offsets, lens, e, rv.n_reads, ix.q,
+                                                 ix.max_read_len, ix.r4, rv.ts, tokens, meta, ctl);
+}
+
+void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
+                             uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st) {
+  uint64_t n = n_cand > n_reads ? n_cand : n_reads;
+  if (n == 0) n = 1;
+  ProfScope ps("check_candidates", st);
+  k_check_candidates<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, cand_off, n_reads, n_cand,
+                                                                  num_bins, ctl);
+}
+
+}  // namespace grim

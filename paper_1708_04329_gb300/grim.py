@@ -1,0 +1,403 @@
+"""Python binding of libgrim.so (``include/grim.h``), argument marshalling only.
+
+Every entry point of the C-ABI has a function of the same name here.  Device
+arrays are torch CUDA tensors (PyTorch supplies device memory and streams);
+host arrays are numpy arrays or CPU tensors.  All computation happens in the
+library's CUDA kernels; there is no CPU fallback: if ``libgrim.so`` cannot be
+built or loaded, importing the library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+GRIM_OK = 0
+GRIM_E_ARG = -1
+GRIM_E_NOMEM = -2
+GRIM_E_CUDA = -3
+GRIM_E_READ_TOO_SHORT = -4
+GRIM_E_READ_TOO_LONG = -5
+GRIM_E_BAD_CANDIDATE = -6
+GRIM_E_OVERFLOW = -7
+GRIM_E_TIMEOUT = -8
+GRIM_E_WORKSPACE = -9
+GRIM_E_NO_LAYOUT = -10
+GRIM_E_UNSUPPORTED = -11
+
+GRIM_LAYOUT_TOKEN_MAJOR = 1
+GRIM_LAYOUT_BIN_MAJOR = 2
+GRIM_LAYOUT_BOTH = 3
+
+#: every symbol include/grim.h declares
+EXPORTS = (
+    "grim_build", "grim_build_host", "grim_index_info", "grim_free", "grim_strerror",
+    "grim_last_cuda_error", "grim_filter_workspace_size", "grim_filter", "grim_filter_host",
+    "grim_loc_to_bin", "grim_edits_for_rate", "grim_profile", "grim_profile_get",
+)
+
+
+class GrimError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = grim_strerror(code)
+        if code == GRIM_E_CUDA:
+            msg += f" ({_lib().grim_last_cuda_error().decode()})"
+        super().__init__(f"{what}: {msg} [{code}]" if what else f"{msg} [{code}]")
+        self.code = code
+
+
+class _Desc(C.Structure):
+    _fields_ = [("ref_len", C.c_uint64), ("num_bins", C.c_uint64), ("num_bins_pad", C.c_uint64),
+                ("B", C.c_uint32), ("q", C.c_uint32), ("ext", C.c_uint32),
+                ("max_read_len", C.c_uint32), ("layouts", C.c_uint32),
+                ("words_per_bin", C.c_uint32), ("token_major", C.c_void_p),
+                ("bin_major", C.c_void_p), ("token_major_bytes", C.c_uint64),
+                ("bin_major_bytes", C.c_uint64)]
+
+
+class _KTime(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
+
+
+_L = None
+
+
+def _lib() -> C.CDLL:
+    """Load libgrim.so (building it in-tree first if it is missing or stale)."""
+    global _L
+    if _L is None:
+        path = _build.build_grim()
+        lib = C.CDLL(str(path))
+        u64, u32, i32, vp = C.c_uint64, C.c_uint32, C.c_int, C.c_void_p
+        pp = C.POINTER(C.c_void_p)
+        lib.grim_build.restype = i32
+        lib.grim_build.argtypes = [vp, u64, u32, u32, u32, u32, vp, pp]
+        lib.grim_build_host.restype = i32
+        lib.grim_build_host.argtypes = [vp, u64, u32, u32, u32, u32, vp, pp]
+        lib.grim_index_info.restype = i32
+        lib.grim_index_info.argtypes = [vp, C.POINTER(_Desc)]
+        lib.grim_free.restype = None
+        lib.grim_free.argtypes = [vp]
+        lib.grim_strerror.restype = C.c_char_p
+        lib.grim_strerror.argtypes = [i32]
+        lib.grim_last_cuda_error.restype = C.c_char_p
+        lib.grim_last_cuda_error.argtypes = []
+        lib.grim_filter_workspace_size.restype = u64
+        lib.grim_filter_workspace_size.argtypes = [vp, u32, u64, u64]
+        fargs = [vp, vp, vp, vp, u32, vp, vp, vp, u64, vp, vp, vp, u64, C.POINTER(C.c_uint64)]
+        lib.grim_filter.restype = i32
+        lib.grim_filter.argtypes = fargs + [vp, u64, vp]
+        lib.grim_filter_host.restype = i32
+        lib.grim_filter_host.argtypes = fargs + [vp]
+        lib.grim_loc_to_bin.restype = u64
+        lib.grim_loc_to_bin.argtypes = [vp, u64]
+        lib.grim_edits_for_rate.restype = u32
+        lib.grim_edits_for_rate.argtypes = [u32, u32, u32]
+        lib.grim_profile.restype = i32
+        lib.grim_profile.argtypes = [i32]
+        lib.grim_profile_get.restype = i32
+        lib.grim_profile_get.argtypes = [C.POINTER(_KTime), i32]
+        _L = lib
+    return _L
+
+
+def library_path() -> str:
+    return str(_build.LIBDIR / "libgrim.so")
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _dptr(t, what: str, esize: int | None = None) -> int:
+    """Device pointer of a contiguous CUDA tensor (or None -> 0)."""
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if esize is not None and t.element_size() != esize:
+        raise ValueError(f"{what} must have {esize}-byte elements")
+    return t.data_ptr()
+
+
+def _hptr(a, what: str, dtype) -> tuple[int, object]:
+    """Host pointer of an array converted to dtype (keeps the buffer alive)."""
+    if a is None:
+        return 0, None
+    if hasattr(a, "numpy") and not isinstance(a, np.ndarray):  # CPU tensor
+        if a.is_cuda:
+            raise ValueError(f"{what} must be host memory")
+        a = a.contiguous()
+        if a.element_size() != np.dtype(dtype).itemsize:
+            raise ValueError(f"{what} must have {np.dtype(dtype).itemsize}-byte elements")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data, arr
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class _CudaArray:
+    """__cuda_array_interface__ view of library-owned device memory."""
+
+    def __init__(self, ptr: int, shape: tuple, typestr: str, owner):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, True),
+                                         "version": 3, "strides": None}
+        self._owner = owner
+
+
+# ---------------------------------------------------------------------------
+# index
+# ---------------------------------------------------------------------------
+
+@dataclass
+class IndexDesc:
+    ref_len: int
+    num_bins: int
+    num_bins_pad: int
+    B: int
+    q: int
+    ext: int
+    max_read_len: int
+    layouts: int
+    words_per_bin: int
+    token_major_ptr: int
+    bin_major_ptr: int
+    token_major_bytes: int
+    bin_major_bytes: int
+
+
+class GrimIndex:
+    """Owns a grim_index handle; grim_free runs when it is closed or collected."""
+
+    def __init__(self, handle: int):
+        self._h = handle
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("index already freed")
+        return self._h
+
+    def close(self) -> None:
+        if self._h:
+            grim_free(self)
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def desc(self) -> IndexDesc:
+        return grim_index_info(self)
+
+    def token_major(self):
+        """Zero-copy uint32 CUDA tensor [4^q, num_bins_pad/32] (None if absent)."""
+        d = self.desc
+        if not d.token_major_ptr:
+            return None
+        torch = _torch()
+        shape = (4 ** d.q, d.num_bins_pad // 32)
+        view = _CudaArray(d.token_major_ptr, shape, "<u4", self)
+        return torch.as_tensor(view, device="cuda")
+
+    def bin_major(self):
+        """Zero-copy uint32 CUDA tensor [num_bins, words_per_bin] (None if absent)."""
+        d = self.desc
+        if not d.bin_major_ptr:
+            return None
+        torch = _torch()
+        view = _CudaArray(d.bin_major_ptr, (d.num_bins, d.words_per_bin), "<u4", self)
+        return torch.as_tensor(view, device="cuda")
+
+
+def grim_build(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_BOTH,
+               stream=None) -> GrimIndex:
+    """grim_build: ``ref`` is a uint8 CUDA tensor of ASCII bases."""
+    h = C.c_void_p()
+    rc = _lib().grim_build(_dptr(ref, "ref", 1), ref.numel(), B, q, max_read_len, layouts,
+                           _stream_ptr(stream), C.byref(h))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_build")
+    return GrimIndex(h.value)
+
+
+def grim_build_host(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_BOTH,
+                    stream=None) -> GrimIndex:
+    """grim_build_host: ``ref`` is host memory (numpy uint8 / CPU tensor)."""
+    p, keep = _hptr(ref, "ref", np.uint8)
+    n = keep.numel() if hasattr(keep, "numel") else keep.size
+    h = C.c_void_p()
+    rc = _lib().grim_build_host(p, n, B, q, max_read_len, layouts, _stream_ptr(stream), C.byref(h))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_build_host")
+    return GrimIndex(h.value)
+
+
+def grim_index_info(index: GrimIndex) -> IndexDesc:
+    d = _Desc()
+    rc = _lib().grim_index_info(index.handle, C.byref(d))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_index_info")
+    return IndexDesc(d.ref_len, d.num_bins, d.num_bins_pad, d.B, d.q, d.ext, d.max_read_len,
+                     d.layouts, d.words_per_bin, d.token_major or 0, d.bin_major or 0,
+                     d.token_major_bytes, d.bin_major_bytes)
+
+
+def grim_free(index: GrimIndex) -> None:
+    if index._h:
+        _lib().grim_free(index._h)
+
+
+def grim_strerror(code: int) -> str:
+    return _lib().grim_strerror(code).decode()
+
+
+def grim_filter_workspace_size(index: GrimIndex, n_reads: int, n_cand: int = 0, cap: int = 0) -> int:
+    return int(_lib().grim_filter_workspace_size(index.handle, n_reads, n_cand, cap))
+
+
+def grim_loc_to_bin(index: GrimIndex, loc: int) -> int:
+    return int(_lib().grim_loc_to_bin(index.handle, loc))
+
+
+def grim_edits_for_rate(L: int, num: int, den: int) -> int:
+    return int(_lib().grim_edits_for_rate(L, num, den))
+
+
+def grim_profile(enable: bool) -> None:
+    _lib().grim_profile(1 if enable else 0)
+
+
+def grim_profile_get() -> dict[str, tuple[int, float]]:
+    """{kernel name: (launches, total ms)} since grim_profile(True)."""
+    lib = _lib()
+    n = lib.grim_profile_get(None, 0)
+    arr = (_KTime * max(n, 1))()
+    n = lib.grim_profile_get(arr, n)
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n)}
+
+
+# ---------------------------------------------------------------------------
+# filter
+# ---------------------------------------------------------------------------
+
+class Workspace:
+    """A reusable device workspace (a uint8 CUDA tensor, 256-byte aligned)."""
+
+    def __init__(self, nbytes: int = 0):
+        self.buf = None
+        self.ensure(nbytes)
+
+    def ensure(self, nbytes: int):
+        torch = _torch()
+        if self.buf is None or self.buf.numel() < nbytes + 256:
+            self.buf = torch.empty(max(nbytes, 1) + 256, dtype=torch.uint8, device="cuda")
+        return self
+
+    def ptr(self) -> int:
+        p = self.buf.data_ptr()
+        return (p + 255) & ~255
+
+    def nbytes(self) -> int:
+        return self.buf.numel() - (self.ptr() - self.buf.data_ptr())
+
+
+def grim_filter(index: GrimIndex, reads, offsets, lens, e, cand=None, cand_off=None,
+                out=None, cap: int | None = None, workspace: Workspace | None = None, stream=None,
+                retry: bool = True):
+    """grim_filter on CUDA tensors.
+
+    reads uint8 [bytes], offsets int64/uint64 [n], lens int32/uint32 [n],
+    e int16/uint16 [n]; cand int32 [n_cand] and cand_off int64/uint64 [n+1]
+    for candidate mode.  ``out`` may be a preallocated (read, bin, count)
+    triple of CUDA tensors of length cap.  Returns (read, bin, count) views of
+    the first n_out records.  With ``retry`` an overflow is retried once with
+    a capacity of exactly n_out.
+    """
+    torch = _torch()
+    n_reads = int(lens.numel())
+    n_cand = int(cand.numel()) if cand is not None else 0
+    user_out = out is not None
+    if out is not None:
+        cap = int(out[0].numel())
+    elif cap is None:
+        cap = 4 * n_reads + 1024
+    if out is None:
+        out = (torch.empty(cap, dtype=torch.int32, device="cuda"),
+               torch.empty(cap, dtype=torch.int32, device="cuda"),
+               torch.empty(cap, dtype=torch.uint8, device="cuda"))
+    ws = workspace or Workspace()
+    ws.ensure(grim_filter_workspace_size(index, n_reads, n_cand, cap))
+    n_out = C.c_uint64(0)
+    rc = _lib().grim_filter(
+        index.handle, _dptr(reads, "reads", 1) if reads.numel() else 0, _dptr(offsets, "offsets", 8),
+        _dptr(lens, "lens", 4), n_reads, _dptr(e, "e", 2), _dptr(cand, "cand", 4),
+        _dptr(cand_off, "cand_off", 8), n_cand, _dptr(out[0], "out_read", 4),
+        _dptr(out[1], "out_bin", 4), _dptr(out[2], "out_count", 1), cap, C.byref(n_out),
+        ws.ptr(), ws.nbytes(), _stream_ptr(stream))
+    if rc == GRIM_E_OVERFLOW and retry and not user_out:
+        return grim_filter(index, reads, offsets, lens, e, cand, cand_off, cap=int(n_out.value),
+                           workspace=ws, stream=stream, retry=False)
+    if rc != GRIM_OK:
+        err = GrimError(rc, "grim_filter")
+        err.n_out = int(n_out.value)
+        raise err
+    n = int(n_out.value)
+    return out[0][:n], out[1][:n], out[2][:n]
+
+
+def grim_filter_host(index: GrimIndex, reads, offsets, lens, e, cand=None, cand_off=None,
+                     cap: int | None = None, out=None, stream=None):
+    """grim_filter_host on host arrays; returns numpy (read, bin, count).
+
+    ``out`` may be a preallocated host (read, bin, count) triple (pinned
+    memory makes the copies asynchronous)."""
+    n_reads = len(lens)
+    n_cand = len(cand) if cand is not None else 0
+    if out is not None:
+        cap = len(out[0])
+        o_r, o_b, o_c = out
+    else:
+        if cap is None:
+            cap = 4 * n_reads + 1024
+        o_r = np.empty(cap, np.uint32)
+        o_b = np.empty(cap, np.uint32)
+        o_c = np.empty(cap, np.uint8)
+    pr, kr = _hptr(reads, "reads", np.uint8)
+    po, ko = _hptr(offsets, "offsets", np.uint64)
+    pl, kl = _hptr(lens, "lens", np.uint32)
+    pe, ke = _hptr(e, "e", np.uint16)
+    pc, kc = _hptr(cand, "cand", np.int32)
+    pco, kco = _hptr(cand_off, "cand_off", np.uint64)
+    pr_o, _ = _hptr(o_r, "out_read", np.uint32)
+    pb_o, _ = _hptr(o_b, "out_bin", np.uint32)
+    pc_o, _ = _hptr(o_c, "out_count", np.uint8)
+    n_out = C.c_uint64(0)
+    rc = _lib().grim_filter_host(index.handle, pr, po, pl, n_reads, pe, pc or None, pco or None,
+                                 n_cand, pr_o, pb_o, pc_o, cap, C.byref(n_out), _stream_ptr(stream))
+    if rc != GRIM_OK:
+        err = GrimError(rc, "grim_filter_host")
+        err.n_out = int(n_out.value)
+        raise err
+    n = int(n_out.value)
+    return o_r[:n], o_b[:n], o_c[:n]

@@ -1,0 +1,51 @@
+"""The C-ABI library builds, loads and exports every symbol include/grim.h
+declares (no compute call: this runs without a GPU)."""
+import re
+import subprocess
+
+import pytest
+
+from tests.conftest import ROOT
+
+
+def _declared() -> set[str]:
+    text = (ROOT / "include" / "grim.h").read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(grim_\w+)\s*\(", text, flags=re.M))
+
+
+def test_header_declares_the_binding_names():
+    from paper_1708_04329_gb300 import grim
+
+    assert _declared() == set(grim.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1708_04329_gb300 import grim
+
+    lib = grim._lib()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", grim.library_path()], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert _declared() <= exported
+
+
+def test_host_helpers_without_gpu():
+    from paper_1708_04329_gb300 import grim
+
+    assert grim.grim_strerror(grim.GRIM_E_OVERFLOW).startswith("more passing records")
+    assert grim.grim_strerror(0) == "ok"
+    # Fig. 4 caption: e = ceil(L * error rate)
+    assert grim.grim_edits_for_rate(100, 5, 100) == 5
+    assert grim.grim_edits_for_rate(150, 5, 100) == 8
+    assert grim.grim_edits_for_rate(250, 5, 100) == 13
+
+
+def test_binding_rejects_host_tensors_before_any_device_call():
+    torch = pytest.importorskip("torch")
+    from paper_1708_04329_gb300 import grim
+
+    with pytest.raises(ValueError):
+        grim._dptr(torch.zeros(4, dtype=torch.uint8), "ref", 1)

@@ -1,0 +1,97 @@
+"""Parity at the full human-scale size, in the launch configuration the
+benchmark times: a 3.1 Gbp repeat-rich genome, B=200, q=5 (15.5M bins, 1.98 GB
+token-major table) and 1,000,000 reads of L=100 with 0-5 edits, e=5, every
+read against every bin in one grim_filter call.
+
+The oracle cannot redo 1.5e15 bit tests, so the GPU's complete output is
+checked on slices the oracle computes exactly -- every bin for a fixed set of
+reads, every read for a fixed range of bins -- plus the bin-major table byte
+for byte, sampled token-major tiles, and properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests.gpu_helpers import build, gpu_filter
+
+pytestmark = [pytest.mark.gpu]
+
+torch = pytest.importorskip("torch")
+
+SAMPLE_READS = 32
+SAMPLE_BINS = 2048
+
+
+@pytest.fixture(scope="module")
+def human():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_04329_gb300 import synth
+
+    w = synth.human_exhaustive()
+    idx = build(w["genome"], w["B"], w["q"], w["max_read_len"])
+    got = gpu_filter(idx, w["reads"], cap=8 * w["reads"].n)
+    oix = oracle.bin_vectors(w["genome"], w["B"], w["q"], w["max_read_len"])
+    yield w, idx, got, oix
+    idx.close()
+
+
+def test_bin_major_table_exact(human):
+    w, idx, _, oix = human
+    bm = idx.bin_major().cpu().numpy().view(np.uint8).reshape(oix.num_bins, -1)
+    assert np.array_equal(bm, oix.vecs)
+
+
+def test_token_major_sampled_tiles(human):
+    w, idx, _, oix = human
+    tm = idx.token_major()
+    n_tiles = idx.desc.num_bins_pad // 1024
+    rng = np.random.default_rng(0)
+    tiles = sorted(set(rng.integers(0, n_tiles, 16).tolist()) | {0, n_tiles - 1})
+    for t in tiles:
+        got = tm[:, t * 32:(t + 1) * 32].cpu().numpy()
+        lo, hi = t * 1024, min((t + 1) * 1024, oix.num_bins)
+        bits = np.unpackbits(oix.vecs[lo:hi], axis=1, bitorder="little").T  # [1024 tokens, bins]
+        full = np.zeros((1024, 1024), np.uint8)
+        full[:, : hi - lo] = bits
+        want = np.packbits(full, axis=1, bitorder="little").view(np.uint32)
+        assert np.array_equal(got, want), t
+
+
+def test_every_bin_for_sampled_reads(human):
+    w, _, got, oix = human
+    rs = w["reads"]
+    idx = np.linspace(0, rs.n - 1, SAMPLE_READS).astype(np.int64)
+    want_r, want_b, want_c = oracle.filter(oix, rs.subset(idx))
+    r, b, c = got
+    for j, ridx in enumerate(idx):
+        sel = r == ridx
+        ws = want_r == j
+        assert np.array_equal(b[sel], want_b[ws]), ridx
+        assert np.array_equal(c[sel], want_c[ws]), ridx
+
+
+def test_every_read_for_a_bin_range(human):
+    w, _, got, oix = human
+    want = oracle.filter(oix, w["reads"], bin_range=(0, SAMPLE_BINS))
+    r, b, c = got
+    sel = b < SAMPLE_BINS
+    assert np.array_equal(r[sel], want[0])
+    assert np.array_equal(b[sel], want[1])
+    assert np.array_equal(c[sel], want[2])
+
+
+def test_properties_at_full_size(human):
+    """Sorted unique output; every planted read passes its true bin (q-gram
+    lemma); exact reads score L-q+1 there; no count exceeds L-q+1."""
+    w, _, got, _ = human
+    rs = w["reads"]
+    r, b, c = got
+    key = r.astype(np.uint64) << np.uint64(32) | b.astype(np.uint64)
+    assert (np.diff(key.astype(np.int64)) > 0).all()
+    assert c.max() <= 96
+    true_key = np.arange(rs.n, dtype=np.uint64) << np.uint64(32) | (rs.true_pos // 200).astype(np.uint64)
+    pos = np.searchsorted(key, true_key)
+    assert (pos < len(key)).all() and (key[pos] == true_key).all()
+    exact = rs.n_edits[np.arange(rs.n)] == 0
+    assert (c[pos[exact]] == 96).all()

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Integer work: every comparison is bit-exact -- tables byte for byte, pass
+lists record for record (read, bin, count) in order.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from tests.conftest import Reads, load_fixture, random_case
+from tests.gpu_helpers import assert_same, build, gpu_filter
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _np(s: str) -> np.ndarray:
+    return np.frombuffer(s.encode(), dtype=np.uint8).copy()
+
+
+def _gpu_tables(idx, q):
+    tm = idx.token_major()
+    bm = idx.bin_major()
+    return (None if tm is None else tm.cpu().numpy(), None if bm is None else bm.cpu().numpy())
+
+
+def _check_tables(ref: np.ndarray, B: int, q: int, mrl: int):
+    idx = build(ref, B, q, mrl)
+    tm, bm = _gpu_tables(idx, q)
+    oix = oracle.bin_vectors(ref, B, q, mrl)
+    vb = oracle.vector_bytes(q)
+    got = bm.view(np.uint8).reshape(oix.num_bins, -1)
+    assert np.array_equal(got[:, :vb], oix.vecs)
+    assert not got[:, vb:].any()
+    assert np.array_equal(tm, oracle.token_major(oix))
+    d = idx.desc
+    assert d.num_bins == oix.num_bins and d.num_bins_pad % 1024 == 0
+    return idx, oix
+
+
+# ---------------------------------------------------------------------------
+# tables (a1-a3)
+# ---------------------------------------------------------------------------
+
+def test_fig2_bits_on_gpu():
+    fx = load_fixture("fig2_q5.txt")
+    idx = build(_np(fx["ref"]), fx["B"], fx["q"], fx["max_read_len"])
+    tm, bm = _gpu_tables(idx, 5)
+    bits = np.unpackbits(bm.view(np.uint8)[0], bitorder="little")
+    assert sorted(np.flatnonzero(bits).tolist()) == sorted(fx["set"])
+    for t in fx["set"]:
+        assert tm[t, 0] & 1
+    for t in fx["clear"]:
+        assert not tm[t, 0] & 1
+
+
+@pytest.mark.parametrize("q", [2, 3, 4, 5, 6])
+def test_tables_match_oracle(q):
+    rng = np.random.default_rng(100 + q)
+    n = int(rng.integers(20_000, 60_000))
+    B = int(rng.integers(7, 40))
+    ref, _, _ = random_case(rng, q, n, B, 50, 0)
+    _check_tables(_np(ref), B, q, int(rng.integers(q, 80)))
+
+
+def test_tables_ragged_and_tiny():
+    # one base shorter than q, a single bin, a window clipped at N
+    for ref, B, q, mrl in [("ACG", 5, 4, 4), ("ACGTA", 5, 4, 10), ("ACGTACGTNNacgtTT", 3, 3, 5)]:
+        _check_tables(_np(ref), B, q, mrl)
+
+
+def test_build_host_equals_build():
+    from paper_1708_04329_gb300 import grim
+
+    g = np.frombuffer(b"ACGT", np.uint8)[np.random.default_rng(3).integers(0, 4, 70_001)]
+    a = build(g, 50, 5, 100)
+    b = grim.grim_build_host(g, 50, 5, 100)
+    assert torch.equal(a.token_major(), b.token_major())
+    assert torch.equal(a.bin_major(), b.bin_major())
+
+
+# ---------------------------------------------------------------------------
+# filter (a4-a8)
+# ---------------------------------------------------------------------------
+
+def test_handworked_fixture_gpu():
+    fx = load_fixture("handworked_q3.txt")
+    rs = Reads([r for r, _ in fx["read"]], [x for _, x in fx["read"]])
+    idx = build(_np(fx["ref"]), fx["B"], fx["q"], fx["max_read_len"])
+    r, b, c = gpu_filter(idx, rs)
+    assert list(zip(r.tolist(), b.tolist(), c.tolist())) == fx["pass"]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_all_bins(seed):
+    """Several 1024-bin tiles plus a ragged one, mixed read lengths, non-bases,
+    per-read e including T <= 0."""
+    rng = np.random.default_rng(500 + seed)
+    q = int(rng.choice([2, 3, 4, 5]))
+    B = int(rng.integers(5, 40))
+    mrl = int(rng.integers(max(q, 20), 120))
+    n = int(rng.integers(30_000, 90_000))
+    ref, reads, e = random_case(rng, q, n, B, mrl, 300)
+    e = [int(x) if rng.random() < 0.9 else 40 for x in e]
+    rs = Reads(reads, e)
+    idx, oix = _check_tables(_np(ref), B, q, mrl)
+    assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_candidates(seed):
+    """Unsorted lists with duplicates and empty lists keep the given order."""
+    rng = np.random.default_rng(700 + seed)
+    q = int(rng.choice([2, 3, 4, 5, 6]))
+    B = int(rng.integers(5, 40))
+    mrl = int(rng.integers(max(q, 20), 120))
+    n = int(rng.integers(20_000, 60_000))
+    ref, reads, e = random_case(rng, q, n, B, mrl, 300)
+    rs = Reads(reads, e)
+    idx, oix = _check_tables(_np(ref), B, q, mrl)
+    nb = oix.num_bins
+    counts = rng.integers(0, 40, len(reads))
+    counts[rng.random(len(reads)) < 0.1] = 0
+    off = np.zeros(len(reads) + 1, np.uint64)
+    off[1:] = np.cumsum(counts)
+    cand = rng.integers(0, nb, int(off[-1])).astype(np.int32)
+    assert_same(gpu_filter(idx, rs, off, cand), oracle.filter(oix, rs, cand_off=off, cand=cand))
+
+
+def test_tiny_plain_full(tiny_plain, tiny_plain_index, tiny_plain_oracle):
+    """The 1 Mbp / 5,000-bin / 2,000-read workload: the whole pass list."""
+    w = tiny_plain
+    idx = build(w["genome"], w["B"], w["q"], w["max_read_len"])
+    assert_same(gpu_filter(idx, w["reads"]), tiny_plain_oracle)
+    from paper_1708_04329_gb300 import synth
+
+    off, cand = synth.candidates((w["reads"].true_pos // w["B"]).astype(np.int32),
+                                 tiny_plain_index.num_bins, seed=4)
+    assert_same(gpu_filter(idx, w["reads"], off, cand),
+                oracle.filter(tiny_plain_index, w["reads"], cand_off=off, cand=cand))
+
+
+def test_many_ranges_per_tile():
+    """Few tiles, many reads: each tile is split into read ranges."""
+    from paper_1708_04329_gb300 import synth
+
+    g = synth.genome(250_000, seed=9)
+    rs = synth.reads(g, 6000, seed=10, e=5, max_edits=5)
+    idx = build(g, 200, 5, 100)
+    oix = oracle.bin_vectors(g, 200, 5, 100)
+    assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
+
+
+def test_threshold_nonpositive_passes_everything():
+    from paper_1708_04329_gb300 import synth
+
+    g = synth.genome(40_000, seed=5)
+    rs = synth.reads(g, 7, seed=6, e=20, max_edits=5)
+    idx = build(g, 100, 5, 100)
+    oix = oracle.bin_vectors(g, 100, 5, 100)
+    got = gpu_filter(idx, rs)
+    assert len(got[0]) == 7 * oix.num_bins
+    assert_same(got, oracle.filter(oix, rs))
+
+
+def test_reads_of_every_length_in_one_call():
+    rng = np.random.default_rng(11)
+    ref, _, _ = random_case(rng, 5, 50_000, 64, 0, 0, dirty=False)
+    g = _np(ref)
+    reads = []
+    for L in range(5, 256):
+        s = int(rng.integers(0, len(ref) - L))
+        reads.append(ref[s:s + L])
+    rs = Reads(reads, [int(x) for x in rng.integers(0, 6, len(reads))])
+    idx = build(g, 64, 5, 255)
+    oix = oracle.bin_vectors(g, 64, 5, 255)
+    assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
+
+
+def test_zero_reads():
+    from paper_1708_04329_gb300 import grim
+
+    idx = build(_np("ACGTACGTAC" * 10), 10, 3, 10)
+    z = torch.zeros(0, dtype=torch.int64, device="cuda")
+    r, b, c = grim.grim_filter(idx, torch.zeros(0, dtype=torch.uint8, device="cuda"), z,
+                               z.to(torch.int32), z.to(torch.int16))
+    assert r.numel() == 0
+
+
+@pytest.mark.parametrize("reads,code", [(["ACGTAC", "AC"], -4), (["ACGTACGTACGT"], -5),
+                                        (["AC", "ACGTACGTACGT"], -4)])
+def test_read_length_errors(reads, code):
+    from paper_1708_04329_gb300 import grim
+
+    idx = build(_np("ACGTACGTAC" * 10), 10, 3, 10)
+    with pytest.raises(grim.GrimError) as ei:
+        gpu_filter(idx, Reads(reads, [0] * len(reads)))
+    assert ei.value.code == code
+
+
+def test_candidate_errors():
+    from paper_1708_04329_gb300 import grim
+
+    idx = build(_np("ACGTACGTAC" * 10), 10, 3, 10)
+    rs = Reads(["ACGTAC", "CGTACG"], [0, 0])
+    with pytest.raises(grim.GrimError) as ei:
+        gpu_filter(idx, rs, np.array([0, 1, 2], np.uint64), np.array([3, 10], np.int32))
+    assert ei.value.code == grim.GRIM_E_BAD_CANDIDATE
+    with pytest.raises(grim.GrimError) as ei:  # decreasing offsets
+        gpu_filter(idx, rs, np.array([0, 2, 1], np.uint64), np.array([3, 4], np.int32))
+    assert ei.value.code == grim.GRIM_E_ARG
+    # an index with only the token-major table cannot serve candidate lists
+    tmo = build(_np("ACGTACGTAC" * 10), 10, 3, 10, layouts=1)
+    with pytest.raises(grim.GrimError) as ei:
+        gpu_filter(tmo, rs, np.array([0, 1, 2], np.uint64), np.array([3, 4], np.int32))
+    assert ei.value.code == grim.GRIM_E_NO_LAYOUT
+
+
+def test_overflow_reports_total_and_count_only():
+    from paper_1708_04329_gb300 import grim, synth
+    from tests.gpu_helpers import dev_reads
+
+    g = synth.genome(40_000, seed=5)
+    rs = synth.reads(g, 50, seed=6, e=5, max_edits=5)
+    idx = build(g, 100, 5, 100)
+    want = oracle.filter(oracle.bin_vectors(g, 100, 5, 100), rs)
+    n = len(want[0])
+    assert n > 3
+    for cap in (0, 3):
+        out = tuple(torch.empty(cap, dtype=dt, device="cuda")
+                    for dt in (torch.int32, torch.int32, torch.uint8))
+        with pytest.raises(grim.GrimError) as ei:
+            grim.grim_filter(idx, **dev_reads(rs), out=out)
+        assert ei.value.code == grim.GRIM_E_OVERFLOW and ei.value.n_out == n
+    # the binding's retry returns the full list
+    assert_same(gpu_filter(idx, rs, cap=1), want)
+
+
+def test_workspace_reuse_is_clean():
+    from paper_1708_04329_gb300 import grim, synth
+
+    g = synth.genome(80_000, seed=7)
+    a = synth.reads(g, 500, seed=8, e=5, max_edits=5)
+    b = synth.reads(g, 300, seed=9, e=3, max_edits=3)
+    idx = build(g, 200, 5, 100)
+    oix = oracle.bin_vectors(g, 200, 5, 100)
+    ws = grim.Workspace()
+    for rs in (a, b, a):
+        assert_same(gpu_filter(idx, rs, workspace=ws), oracle.filter(oix, rs))
+
+
+def test_filter_host_equals_oracle():
+    from paper_1708_04329_gb300 import grim, synth
+
+    g = synth.genome(80_000, seed=12)
+    rs = synth.reads(g, 400, seed=13, e=5, max_edits=5)
+    idx = build(g, 200, 5, 100)
+    oix = oracle.bin_vectors(g, 200, 5, 100)
+    got = grim.grim_filter_host(idx, rs.seq, rs.offsets, rs.lens, rs.e)
+    assert_same(got, oracle.filter(oix, rs))
+    off, cand = synth.candidates((rs.true_pos // 200).astype(np.int32), oix.num_bins, seed=3)
+    got = grim.grim_filter_host(idx, rs.seq, rs.offsets, rs.lens, rs.e, cand=cand, cand_off=off)
+    assert_same(got, oracle.filter(oix, rs, cand_off=off, cand=cand))
+
+
+def test_q6_all_bins_reports_unsupported():
+    from paper_1708_04329_gb300 import grim
+
+    idx = build(_np("ACGTACGTACGT" * 20), 10, 6, 12)
+    with pytest.raises(grim.GrimError) as ei:
+        gpu_filter(idx, Reads(["ACGTACGT"], [0]))
+    assert ei.value.code == grim.GRIM_E_UNSUPPORTED
