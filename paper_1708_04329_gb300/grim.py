@@ -157,7 +157,7 @@ class _CudaArray:
     """__cuda_array_interface__ view of library-owned device memory."""
 
     def __init__(self, ptr: int, shape: tuple, typestr: str, owner):
-        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, True),
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False),
                                          "version": 3, "strides": None}
         self._owner = owner
 
@@ -211,22 +211,25 @@ class GrimIndex:
         return grim_index_info(self)
 
     def token_major(self):
-        """Zero-copy uint32 CUDA tensor [4^q, num_bins_pad/32] (None if absent)."""
+        """Zero-copy CUDA tensor [4^q, num_bins_pad/32] of the table's uint32
+        words, typed int32 (torch's fully supported 32-bit type; view the host
+        copy as uint32).  None if the index has no token-major table."""
         d = self.desc
         if not d.token_major_ptr:
             return None
         torch = _torch()
         shape = (4 ** d.q, d.num_bins_pad // 32)
-        view = _CudaArray(d.token_major_ptr, shape, "<u4", self)
+        view = _CudaArray(d.token_major_ptr, shape, "<i4", self)
         return torch.as_tensor(view, device="cuda")
 
     def bin_major(self):
-        """Zero-copy uint32 CUDA tensor [num_bins, words_per_bin] (None if absent)."""
+        """Zero-copy CUDA tensor [num_bins, words_per_bin] of the table's uint32
+        words, typed int32.  None if the index has no bin-major table."""
         d = self.desc
         if not d.bin_major_ptr:
             return None
         torch = _torch()
-        view = _CudaArray(d.bin_major_ptr, (d.num_bins, d.words_per_bin), "<u4", self)
+        view = _CudaArray(d.bin_major_ptr, (d.num_bins, d.words_per_bin), "<i4", self)
         return torch.as_tensor(view, device="cuda")
 
 

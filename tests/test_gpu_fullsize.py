@@ -49,7 +49,7 @@ def test_token_major_sampled_tiles(human):
     rng = np.random.default_rng(0)
     tiles = sorted(set(rng.integers(0, n_tiles, 16).tolist()) | {0, n_tiles - 1})
     for t in tiles:
-        got = tm[:, t * 32:(t + 1) * 32].cpu().numpy()
+        got = tm[:, t * 32:(t + 1) * 32].contiguous().cpu().numpy().view(np.uint32)
         lo, hi = t * 1024, min((t + 1) * 1024, oix.num_bins)
         bits = np.unpackbits(oix.vecs[lo:hi], axis=1, bitorder="little").T  # [1024 tokens, bins]
         full = np.zeros((1024, 1024), np.uint8)
