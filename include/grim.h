@@ -170,6 +170,38 @@ int grim_filter_host(const grim_index* idx, const char* reads, const uint64_t* o
                      uint32_t* out_read, uint32_t* out_bin, uint8_t* out_count, uint64_t cap,
                      uint64_t* n_out, void* stream);
 
+/*
+ * As grim_filter, for callers that cannot allocate device memory: a host
+ * process whose memory manager owns the whole GPU, or a serving loop that
+ * keeps cudaMalloc / cudaFree (which can synchronise the device) off its
+ * request path.  The paper has no counterpart to this entry point.
+ *
+ * The scratch the filter needs lives in one fixed device array of
+ * GRIM_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits; the call allocates nothing.
+ * The caller still passes the inputs and the output arrays (device memory),
+ * exactly as for grim_filter.
+ *   - Size limit: a call whose scratch (grim_filter_workspace_size(idx,
+ *     n_reads, n_cand, cap)) exceeds GRIM_NOALLOC_SCRATCH_BYTES is rejected
+ *     with GRIM_E_WORKSPACE before any device work (at q = 5 and 100 bp
+ *     reads that is roughly 196 bytes per read plus 18 bytes per unit of
+ *     cap).
+ *   - First call on a device: it looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - Sharing: all calls share the one array and it keeps the last call's
+ *     contents (each call clears what must start at zero).  Calls that
+ *     overlap on the GPU -- from several host threads, or on several
+ *     streams -- race on it; serialise them.
+ * Errors: as grim_filter.
+ */
+#define GRIM_NOALLOC_SCRATCH_BYTES (32u << 20)
+int grim_filter_noalloc(const grim_index* idx, const char* reads, const uint64_t* offsets,
+                        const uint32_t* lens, uint32_t n_reads, const uint16_t* e,
+                        const int32_t* cand, const uint64_t* cand_off, uint64_t n_cand,
+                        uint32_t* out_read, uint32_t* out_bin, uint8_t* out_count, uint64_t cap,
+                        uint64_t* n_out, void* stream);
+
 /* ---- helpers of the mapper around the filter (§GRIM-Filter, Fig. 5) ----- */
 
 /* Bin whose core holds reference position `loc`: loc / B. */

@@ -28,6 +28,7 @@ GRIM_SOURCES = [
     "grim_exhaustive.cu",
     "grim_candidates.cu",
     "grim_compact.cu",
+    "grim_noalloc.cu",
 ]
 GRIM_HEADERS = ["grim_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

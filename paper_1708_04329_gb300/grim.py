@@ -37,6 +37,7 @@ EXPORTS = (
     "grim_build", "grim_build_host", "grim_index_info", "grim_free", "grim_strerror",
     "grim_last_cuda_error", "grim_filter_workspace_size", "grim_filter", "grim_filter_host",
     "grim_loc_to_bin", "grim_edits_for_rate", "grim_profile", "grim_profile_get",
+    "grim_filter_noalloc",
 )
 
 
@@ -92,6 +93,8 @@ def _lib() -> C.CDLL:
         lib.grim_filter.argtypes = fargs + [vp, u64, vp]
         lib.grim_filter_host.restype = i32
         lib.grim_filter_host.argtypes = fargs + [vp]
+        lib.grim_filter_noalloc.restype = i32
+        lib.grim_filter_noalloc.argtypes = fargs + [vp]
         lib.grim_loc_to_bin.restype = u64
         lib.grim_loc_to_bin.argtypes = [vp, u64]
         lib.grim_edits_for_rate.restype = u32
@@ -404,3 +407,36 @@ def grim_filter_host(index: GrimIndex, reads, offsets, lens, e, cand=None, cand_
         raise err
     n = int(n_out.value)
     return o_r[:n], o_b[:n], o_c[:n]
+
+
+#: bytes of the fixed device scratch array grim_filter_noalloc uses
+GRIM_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def grim_filter_noalloc(index: GrimIndex, reads, offsets, lens, e, out, cand=None, cand_off=None,
+                        stream=None):
+    """grim_filter_noalloc on CUDA tensors: the filter without any device
+    allocation, for callers that cannot allocate (a process whose memory
+    manager owns the whole GPU, or a serving loop that keeps cudaMalloc off
+    its request path).  Scratch comes from one fixed array inside the library
+    (``GRIM_NOALLOC_SCRATCH_BYTES``), shared by all calls: calls must not
+    overlap on the GPU.  ``out`` is the caller's (read, bin, count) triple of
+    CUDA tensors; returns views of its first n_out records.  Raises
+    GrimError(GRIM_E_WORKSPACE) when the call needs more scratch than the
+    array holds."""
+    n_reads = int(lens.numel())
+    n_cand = int(cand.numel()) if cand is not None else 0
+    cap = int(out[0].numel())
+    n_out = C.c_uint64(0)
+    rc = _lib().grim_filter_noalloc(
+        index.handle, _dptr(reads, "reads", 1) if reads.numel() else 0, _dptr(offsets, "offsets", 8),
+        _dptr(lens, "lens", 4), n_reads, _dptr(e, "e", 2), _dptr(cand, "cand", 4),
+        _dptr(cand_off, "cand_off", 8), n_cand, _dptr(out[0], "out_read", 4),
+        _dptr(out[1], "out_bin", 4), _dptr(out[2], "out_count", 1), cap, C.byref(n_out),
+        _stream_ptr(stream))
+    if rc != GRIM_OK:
+        err = GrimError(rc, "grim_filter_noalloc")
+        err.n_out = int(n_out.value)
+        raise err
+    n = int(n_out.value)
+    return out[0][:n], out[1][:n], out[2][:n]
