@@ -186,6 +186,7 @@ def run_native(args, rank, world, local):
     def step():
         idx = grim.grim_build(ref, B, q, mrl, grim.GRIM_LAYOUT_BOTH, stream=st)
         a = grim.grim_filter(idx, **dev, out=outs[0], workspace=ws, stream=st)
+        counts["stats"] = grim.grim_last_filter_stats()
         b = grim.grim_filter(idx, **dev, cand=cand, cand_off=cand_off, out=outs[1], workspace=ws,
                              stream=st)
         counts["all"], counts["cand"] = int(a[0].numel()), int(b[0].numel())
@@ -233,11 +234,17 @@ def run_native(args, rank, world, local):
     peak_tbit = n_sm * 1024 * sm_max * 1e6 / 1e12
     achieved_tbit = bit_tests / (per_launch_ms / 1e3) / 1e12
     traffic = None
+    stats = counts.pop("stats")
+    executed = stats["tokens_executed"] * 1024  # bit tests the kernel actually performed
+    executed_tbit = executed / (per_launch_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved_tbit, 2), "peak": round(peak_tbit, 2),
                 "unit": "Tbit-tests/s", "frac": round(achieved_tbit / peak_tbit, 4),
                 "traffic": traffic,
                 "kernel": "k_exhaustive", "kernel_ms": round(per_launch_ms, 3),
-                "peak_basis": f"{n_sm} SMs x 128 B/clk shared-memory loads x 8 bits x {sm_max:.0f} MHz"}
+                "peak_basis": f"{n_sm} SMs x 128 B/clk shared-memory loads x 8 bits x {sm_max:.0f} MHz",
+                "algorithmic_bit_tests": bit_tests, "executed_bit_tests": executed,
+                "executed_tbit_per_s": round(executed_tbit, 2),
+                "executed_frac": round(executed_tbit / peak_tbit, 4)}
 
     stages = {k: round(v[1] / max(v[0], 1), 3) for k, v in prof.items()}
     launches = int(sum(v[0] for v in prof.values()))

@@ -211,6 +211,20 @@ uint64_t grim_loc_to_bin(const grim_index* idx, uint64_t loc);
  * (Fig. 4 caption: the ceiling of read length times the error rate). */
 uint32_t grim_edits_for_rate(uint32_t L, uint32_t num, uint32_t den);
 
+/* ---- work counters of the last filter call ------------------------------ */
+typedef struct {
+  uint64_t n_reads;          /* reads in the call                                     */
+  uint64_t n_records;        /* passing records found (may exceed the call's cap)     */
+  uint64_t pairs;            /* (read, bin) pairs decided: reads x bins, or n_cand    */
+  uint64_t tokens_executed;  /* all-bins mode: read tokens applied to 1024-bin tiles,
+                                counting padding up to a 16-token block; stops early
+                                for a read once every bin of the tile has failed      */
+} grim_filter_stats;
+
+/* Counters of the calling thread's last successful grim_filter /
+ * grim_filter_host / grim_filter_noalloc call. */
+int grim_last_filter_stats(grim_filter_stats* out);
+
 /* ---- per-kernel timing -------------------------------------------------- */
 typedef struct {
   char name[32];      /* kernel name                                 */

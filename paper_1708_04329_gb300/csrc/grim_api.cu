@@ -19,6 +19,7 @@ namespace grim {
 namespace {
 
 thread_local std::string g_cuda_err;
+thread_local grim_filter_stats g_last_stats{};
 
 int cuda_fail(cudaError_t e) {
   g_cuda_err = cudaGetErrorString(e);
@@ -353,6 +354,10 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   prof_collect();
+  g_last_stats.n_reads = n_reads;
+  g_last_stats.n_records = h.n_rec;
+  g_last_stats.pairs = cand_mode ? n_cand : (uint64_t)n_reads * v.num_bins;
+  g_last_stats.tokens_executed = h.blocks * kBlockTokens;
   return GRIM_OK;
 }
 
@@ -425,6 +430,12 @@ uint64_t grim_loc_to_bin(const grim_index* idx, uint64_t loc) { return idx ? loc
 uint32_t grim_edits_for_rate(uint32_t L, uint32_t num, uint32_t den) {
   if (den == 0) return 0;
   return (uint32_t)(((uint64_t)L * num + den - 1) / den);
+}
+
+int grim_last_filter_stats(grim_filter_stats* out) {
+  if (!out) return GRIM_E_ARG;
+  *out = g_last_stats;
+  return GRIM_OK;
 }
 
 int grim_profile(int enable) {

@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
 
     // per-group state (identical in the group's 8 lanes)
     uint32_t cur = kNone, blk = 0, nblk = 0, ntok = 0, bias = 0;
+    uint32_t executed = 0;  // blocks this group applied to real reads
     bool fin = false;
     const uint16_t* tk = a.rv.tokens + (uint64_t)r0 * a.rv.ts;  // any in-bounds block
     Counters c;
@@ -251,7 +252,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
         const uint32_t tw[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
         add_block(c, tw, lane_row);
       }
-      if (!fin) ++blk;
+      if (!fin) {
+        ++blk;
+        ++executed;
+      }
 
       // (3) a read ends when every bin of its tile is dead or its tokens are used up
       const uint32_t all_dead = c.dead[0] & c.dead[1] & c.dead[2] & c.dead[3];
@@ -295,6 +299,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
       }
       if (done) cur = kNone;
     }
+    // one count per group (its 8 lanes agree), one atomic per warp and item
+    uint32_t ex = li == 0 ? executed : 0u;
+    ex = __reduce_add_sync(0xFFFFFFFFu, ex);
+    if (lane == 0 && ex) atomicAdd(&a.ctl->blocks, (unsigned long long)ex);
   }
 }
 

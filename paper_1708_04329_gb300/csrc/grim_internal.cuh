@@ -20,11 +20,11 @@ constexpr uint32_t kMaxTokens = 255;     // counts are uint8
 
 // Device control block at the start of the filter workspace.
 struct Ctl {
-  unsigned long long n_rec;  // passing records found (may exceed cap)
-  uint32_t status;           // kStatus* bits
-  uint32_t item;             // work-item counter of the persistent filter kernels
-  uint32_t max_mult_bits;    // unused slot kept for alignment
-  uint32_t pad[59];
+  unsigned long long n_rec;   // passing records found (may exceed cap)
+  uint32_t status;            // kStatus* bits
+  uint32_t item;              // work-item counter of the persistent filter kernels
+  unsigned long long blocks;  // 16-token blocks applied to 1024-bin tiles (all-bins mode)
+  uint32_t pad[58];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte slot");
 

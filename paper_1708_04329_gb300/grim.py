@@ -37,7 +37,7 @@ EXPORTS = (
     "grim_build", "grim_build_host", "grim_index_info", "grim_free", "grim_strerror",
     "grim_last_cuda_error", "grim_filter_workspace_size", "grim_filter", "grim_filter_host",
     "grim_loc_to_bin", "grim_edits_for_rate", "grim_profile", "grim_profile_get",
-    "grim_filter_noalloc",
+    "grim_filter_noalloc", "grim_last_filter_stats",
 )
 
 
@@ -57,6 +57,11 @@ class _Desc(C.Structure):
                 ("words_per_bin", C.c_uint32), ("token_major", C.c_void_p),
                 ("bin_major", C.c_void_p), ("token_major_bytes", C.c_uint64),
                 ("bin_major_bytes", C.c_uint64)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("n_reads", C.c_uint64), ("n_records", C.c_uint64), ("pairs", C.c_uint64),
+                ("tokens_executed", C.c_uint64)]
 
 
 class _KTime(C.Structure):
@@ -99,6 +104,8 @@ def _lib() -> C.CDLL:
         lib.grim_loc_to_bin.argtypes = [vp, u64]
         lib.grim_edits_for_rate.restype = u32
         lib.grim_edits_for_rate.argtypes = [u32, u32, u32]
+        lib.grim_last_filter_stats.restype = i32
+        lib.grim_last_filter_stats.argtypes = [C.POINTER(_Stats)]
         lib.grim_profile.restype = i32
         lib.grim_profile.argtypes = [i32]
         lib.grim_profile_get.restype = i32
@@ -288,6 +295,15 @@ def grim_loc_to_bin(index: GrimIndex, loc: int) -> int:
 
 def grim_edits_for_rate(L: int, num: int, den: int) -> int:
     return int(_lib().grim_edits_for_rate(L, num, den))
+
+
+def grim_last_filter_stats() -> dict:
+    """Work counters of this thread's last successful filter call."""
+    st = _Stats()
+    rc = _lib().grim_last_filter_stats(C.byref(st))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_last_filter_stats")
+    return {f: int(getattr(st, f)) for f, _ in _Stats._fields_}
 
 
 def grim_profile(enable: bool) -> None:
