@@ -59,6 +59,17 @@ extern "C" {
 /* Bin-major: bin b's 4^q-bit vector is contiguous (Fig. 2 column).  Used by
  * the candidate-list filter. */
 #define GRIM_LAYOUT_BIN_MAJOR 2u
+/* Coarse token-major: the token-major layout over super-bins of
+ * GRIM_COARSE_FACTOR adjacent bins.  A super-bin's window is the union of its
+ * bins' windows, and because ext >= q-1 every q-gram of that union lies wholly
+ * inside one member's window, so a super-bin's vector is exactly the OR of its
+ * members' vectors and its token sum bounds each member's from above.  With
+ * this layout and the bin-major one, the all-bins filter first discards
+ * super-bins whose sum is below T, then checks the members of the rest
+ * exactly against the bin-major table; the result is identical. */
+#define GRIM_LAYOUT_COARSE 4u
+#define GRIM_LAYOUT_ALL 7u
+#define GRIM_COARSE_FACTOR 2u
 
 typedef struct grim_index grim_index; /* opaque; owns its device tables */
 
@@ -78,6 +89,11 @@ typedef struct {
    * b is bit (t % 32) of word t / 32.  NULL if absent. */
   const uint32_t* bin_major;
   uint64_t token_major_bytes, bin_major_bytes;
+  /* coarse token-major table, device, uint32[4^q][num_coarse_pad / 32] over
+   * super-bins s = bins [s*coarse_factor, (s+1)*coarse_factor); NULL if absent */
+  const uint32_t* coarse_token_major;
+  uint64_t num_coarse, num_coarse_pad, coarse_token_major_bytes;
+  uint32_t coarse_factor;
 } grim_index_desc;
 
 /*
@@ -184,8 +200,9 @@ int grim_filter_host(const grim_index* idx, const char* reads, const uint64_t* o
  *   - Size limit: a call whose scratch (grim_filter_workspace_size(idx,
  *     n_reads, n_cand, cap)) exceeds GRIM_NOALLOC_SCRATCH_BYTES is rejected
  *     with GRIM_E_WORKSPACE before any device work (at q = 5 and 100 bp
- *     reads that is roughly 196 bytes per read plus 18 bytes per unit of
- *     cap).
+ *     reads that is roughly 196 bytes per read plus 18 bytes per unit of cap,
+ *     or, for an index with the coarse layout, roughly 1.9 kB per read while
+ *     cap stays below 64 records per read).
  *   - First call on a device: it looks up the array's device address (once
  *     per device, with that device current); make that first call before
  *     any stream capture.
@@ -216,9 +233,11 @@ typedef struct {
   uint64_t n_reads;          /* reads in the call                                     */
   uint64_t n_records;        /* passing records found (may exceed the call's cap)     */
   uint64_t pairs;            /* (read, bin) pairs decided: reads x bins, or n_cand    */
-  uint64_t tokens_executed;  /* all-bins mode: read tokens applied to 1024-bin tiles,
-                                counting padding up to a 16-token block; stops early
-                                for a read once every bin of the tile has failed      */
+  uint64_t tokens_executed;  /* all-bins mode: read tokens applied to 1024-(super-)bin
+                                tiles, counting padding up to a 16-token block; stops
+                                early for a read once every bin of the tile has failed */
+  uint64_t survivors;        /* all-bins mode, coarse-then-exact: (read, super-bin)
+                                pairs that passed the coarse pass (0 otherwise)       */
 } grim_filter_stats;
 
 /* Counters of the calling thread's last successful grim_filter /

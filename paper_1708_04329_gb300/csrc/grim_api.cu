@@ -2,6 +2,7 @@
 // workspace layout, the order of kernel launches, status reporting and the
 // optional per-kernel event timing.
 #include <mutex>
+#include <stddef.h>
 #include <string.h>
 #include <string>
 #include <vector>
@@ -9,10 +10,12 @@
 #include "grim_internal.cuh"
 
 struct grim_index {
-  grim::IndexView v;
+  grim::IndexView v;   // bins: token-major and bin-major tables
+  grim::IndexView cv;  // super-bins of GRIM_COARSE_FACTOR bins: coarse token-major table
   uint32_t layouts;
   uint32_t* tm;
   uint32_t* bm;
+  uint32_t* ctm;
 };
 
 namespace grim {
@@ -41,28 +44,50 @@ inline uint32_t token_stride(const IndexView& v) {
 }
 
 struct Layout {
-  uint64_t tok, meta, keys_a, keys_b, cnt_a, cnt_b, hist, total;
+  uint64_t tok, meta, keys_a, keys_b, cnt_a, cnt_b, hist, cand, cand_off, total;
 };
 
-Layout layout(const IndexView& v, uint32_t n_reads, uint64_t cap) {
+// Survivors of the coarse pass get their own capacity: reads from repeat
+// families survive in many super-bins that then fail the exact check.
+constexpr uint64_t kSurvivorsPerRead = 64;
+
+inline uint64_t record_capacity(uint32_t n_reads, uint64_t cap, uint32_t coarse_factor) {
+  const uint64_t s = coarse_factor ? kSurvivorsPerRead * n_reads : 0;
+  return s > cap ? s : cap;
+}
+
+// coarse_factor > 0: room for the coarse pass's survivors and for the
+// candidate lists they expand into (coarse_factor per survivor)
+Layout layout(const IndexView& v, uint32_t n_reads, uint64_t cap, uint32_t coarse_factor) {
   Layout L{};
+  const uint64_t rcap = record_capacity(n_reads, cap, coarse_factor);
   uint64_t o = sizeof(Ctl);
   L.tok = o;
   o = align256(o + (uint64_t)n_reads * token_stride(v) * sizeof(uint16_t));
   L.meta = o;
   o = align256(o + (uint64_t)n_reads * sizeof(uint32_t));
   L.keys_a = o;
-  o = align256(o + cap * sizeof(unsigned long long));
+  o = align256(o + rcap * sizeof(unsigned long long));
   L.keys_b = o;
-  o = align256(o + cap * sizeof(unsigned long long));
+  o = align256(o + rcap * sizeof(unsigned long long));
   L.cnt_a = o;
-  o = align256(o + cap);
+  o = align256(o + rcap);
   L.cnt_b = o;
-  o = align256(o + cap);
+  o = align256(o + rcap);
   L.hist = o;
-  o = align256(o + sort_workspace_bytes(cap));
+  o = align256(o + sort_workspace_bytes(rcap));
+  L.cand = o;
+  o = align256(o + (coarse_factor ? rcap * coarse_factor * sizeof(int32_t) : 0));
+  L.cand_off = o;
+  o = align256(o + (coarse_factor ? ((uint64_t)n_reads + 1) * sizeof(uint64_t) : 0));
   L.total = o;
   return L;
+}
+
+// the all-bins filter can run coarse-then-exact when the index has both the
+// coarse table and the bin-major table
+bool two_level_capable(const grim_index* idx) {
+  return (idx->layouts & GRIM_LAYOUT_COARSE) && (idx->layouts & GRIM_LAYOUT_BIN_MAJOR);
 }
 
 int status_to_code(uint32_t s) {
@@ -173,7 +198,7 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
   if (!out) return GRIM_E_ARG;
   *out = nullptr;
   if (!ref || len == 0 || B == 0 || max_read_len < q || layouts == 0 ||
-      (layouts & ~(GRIM_LAYOUT_TOKEN_MAJOR | GRIM_LAYOUT_BIN_MAJOR)))
+      (layouts & ~GRIM_LAYOUT_ALL))
     return GRIM_E_ARG;
   if (q < 2 || q > 6 || max_read_len - q + 1 > kMaxTokens) return GRIM_E_UNSUPPORTED;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -189,6 +214,14 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
   v.num_bins_pad = (v.num_bins + kTileBins - 1) / kTileBins * kTileBins;
   v.wpad = v.num_bins_pad / 32;
   if (v.num_bins > 0xFFFFFFFFull) return GRIM_E_UNSUPPORTED;  // bins are uint32 in the output
+  // super-bins: core f*B, the same extension (window = union of f bins' windows)
+  IndexView cv = v;
+  cv.B = v.B * GRIM_COARSE_FACTOR;
+  cv.num_bins = (len + cv.B - 1) / cv.B;
+  cv.num_bins_pad = (cv.num_bins + kTileBins - 1) / kTileBins * kTileBins;
+  cv.wpad = cv.num_bins_pad / 32;
+  // bin-major vectors padded with zero vectors to whole super-bins
+  const uint64_t bm_bins = cv.num_bins * GRIM_COARSE_FACTOR;
 
   grim_index* ix = new (std::nothrow) grim_index{};
   if (!ix) return GRIM_E_NOMEM;
@@ -196,6 +229,7 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
   auto fail = [&](int code) {
     cudaFree(ix->tm);
     cudaFree(ix->bm);
+    cudaFree(ix->ctm);
     delete ix;
     return code;
   };
@@ -205,12 +239,19 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
     if (e != cudaSuccess) return fail(cuda_fail(e));
   }
   if (layouts & GRIM_LAYOUT_BIN_MAJOR) {
-    e = cudaMalloc(&ix->bm, v.num_bins * v.wpb * sizeof(uint32_t));
+    e = cudaMalloc(&ix->bm, bm_bins * v.wpb * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+  }
+  if (layouts & GRIM_LAYOUT_COARSE) {
+    e = cudaMalloc(&ix->ctm, (uint64_t)cv.r4 * cv.wpad * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(cuda_fail(e));
   }
   v.tm = ix->tm;
   v.bm = ix->bm;
   ix->v = v;
+  cv.tm = ix->ctm;
+  cv.bm = nullptr;
+  ix->cv = cv;
 
   // packed reference (one spare word at the end of each array for the
   // two-word reads of the token extraction)
@@ -227,7 +268,13 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
   cudaMemsetAsync(invalid + n32, 0xFF, 2 * sizeof(uint32_t), st);
   launch_pack_ref(ref, len, codes, invalid, st);
   if (ix->tm) launch_build_token_major(codes, invalid, v, ix->tm, st);
-  if (ix->bm) launch_build_bin_major(codes, invalid, v, ix->bm, st);
+  if (ix->ctm) launch_build_token_major(codes, invalid, cv, ix->ctm, st);
+  if (ix->bm) {
+    if (bm_bins > v.num_bins)
+      cudaMemsetAsync(ix->bm + v.num_bins * v.wpb, 0,
+                      (bm_bins - v.num_bins) * v.wpb * sizeof(uint32_t), st);
+    launch_build_bin_major(codes, invalid, v, ix->bm, st);
+  }
   cudaFreeAsync(codes, st);
   cudaFreeAsync(invalid, st);
   e = cudaGetLastError();
@@ -279,6 +326,12 @@ int grim_index_info(const grim_index* idx, grim_index_desc* out) {
   out->bin_major = idx->bm;
   out->token_major_bytes = idx->tm ? (uint64_t)v.r4 * v.wpad * sizeof(uint32_t) : 0;
   out->bin_major_bytes = idx->bm ? v.num_bins * v.wpb * sizeof(uint32_t) : 0;
+  out->coarse_token_major = idx->ctm;
+  out->num_coarse = idx->cv.num_bins;
+  out->num_coarse_pad = idx->cv.num_bins_pad;
+  out->coarse_token_major_bytes =
+      idx->ctm ? (uint64_t)idx->cv.r4 * idx->cv.wpad * sizeof(uint32_t) : 0;
+  out->coarse_factor = GRIM_COARSE_FACTOR;
   return GRIM_OK;
 }
 
@@ -286,6 +339,7 @@ void grim_free(grim_index* idx) {
   if (!idx) return;
   cudaFree(idx->tm);
   cudaFree(idx->bm);
+  cudaFree(idx->ctm);
   delete idx;
 }
 
@@ -293,7 +347,7 @@ uint64_t grim_filter_workspace_size(const grim_index* idx, uint32_t n_reads, uin
                                     uint64_t cap) {
   (void)n_cand;
   if (!idx) return 0;
-  return layout(idx->v, n_reads, cap).total;
+  return layout(idx->v, n_reads, cap, two_level_capable(idx) ? GRIM_COARSE_FACTOR : 0).total;
 }
 
 int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offsets,
@@ -306,15 +360,17 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   const bool cand_mode = cand != nullptr || cand_off != nullptr;
   if (cand_mode && !cand_off) return GRIM_E_ARG;
   if (cand_mode && n_cand && !cand) return GRIM_E_ARG;
+  const bool capable = two_level_capable(idx);
   if (cand_mode && !(idx->layouts & GRIM_LAYOUT_BIN_MAJOR)) return GRIM_E_NO_LAYOUT;
-  if (!cand_mode && !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR)) return GRIM_E_NO_LAYOUT;
+  if (!cand_mode && !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR) && !capable) return GRIM_E_NO_LAYOUT;
   if (!cand_mode && idx->v.q > 5) return GRIM_E_UNSUPPORTED;
   if (n_reads == 0) return GRIM_OK;
   if (!reads || !offsets || !lens || !e) return GRIM_E_ARG;
   if (cap && (!out_read || !out_bin || !out_count)) return GRIM_E_ARG;
   if (cap > 0xFFFFFFFFull) return GRIM_E_ARG;
   const IndexView& v = idx->v;
-  const Layout L = layout(v, n_reads, cap);
+  const uint32_t f = capable ? GRIM_COARSE_FACTOR : 0;
+  const Layout L = layout(v, n_reads, cap, f);
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return GRIM_E_ARG;
   if (workspace_bytes < L.total) return GRIM_E_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -322,35 +378,90 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   Ctl* ctl = reinterpret_cast<Ctl*>(ws);
   uint16_t* tokens = reinterpret_cast<uint16_t*>(ws + L.tok);
   uint32_t* meta = reinterpret_cast<uint32_t*>(ws + L.meta);
+  // record buffers hold rcap >= cap records; more than cap final records is
+  // still an overflow of the caller's arrays
+  const uint64_t rcap = record_capacity(n_reads, cap, f);
   RecordsView ra{reinterpret_cast<unsigned long long*>(ws + L.keys_a),
-                 reinterpret_cast<uint8_t*>(ws + L.cnt_a), cap};
+                 reinterpret_cast<uint8_t*>(ws + L.cnt_a), rcap};
   RecordsView rb{reinterpret_cast<unsigned long long*>(ws + L.keys_b),
-                 reinterpret_cast<uint8_t*>(ws + L.cnt_b), cap};
+                 reinterpret_cast<uint8_t*>(ws + L.cnt_b), rcap};
   ReadsView rv{tokens, meta, n_reads, token_stride(v)};
   const uint32_t bin_bits = v.num_bins > 1 ? bit_length(v.num_bins - 1) : 0;
+  uint64_t survivors = 0;
+  const uint32_t read_bits = n_reads > 1 ? bit_length((uint64_t)n_reads - 1) : 0;
 
   CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
   launch_tokenise(reads, offsets, lens, e, v, rv, tokens, meta, ctl, st);
-  if (cand_mode) {
-    launch_check_candidates(cand, cand_off, n_reads, n_cand, v.num_bins, ctl, st);
-    launch_candidates(v, rv, cand, cand_off, ra, ctl, st);
-  } else {
-    launch_exhaustive(v, rv, ra, bin_bits, ctl, st);
-  }
+  if (cand_mode) launch_check_candidates(cand, cand_off, n_reads, n_cand, v.num_bins, ctl, st);
   CK(cudaGetLastError());
+  // input errors end the call before the filter runs; the batch's largest
+  // miss budget sizes the all-bins kernel's counters
   Ctl h{};
   CK(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  int sc = status_to_code(h.status);
+  if (sc != GRIM_OK) {
+    prof_collect();
+    return sc;
+  }
+
+  // what the final sort and split work from
+  const int32_t* lists = cand;
+  const uint64_t* lists_off = cand_off;
+  uint64_t n_lists = n_cand;
+  bool list_mode = cand_mode;
+
+  if (cand_mode) {
+    launch_candidates(v, rv, cand, cand_off, ra, ctl, st);
+  } else {
+    // all bins: coarse-then-exact when the index allows it and the budget is
+    // small enough for super-bins to fail early; otherwise one exact pass
+    bool two = capable && (h.max_d < 32 || !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR));
+    if (two) {
+      const IndexView& cv = idx->cv;
+      const uint32_t cbits = cv.num_bins > 1 ? bit_length(cv.num_bins - 1) : 0;
+      launch_exhaustive(cv, rv, ra, cbits, h.max_d, ctl, st, "exhaustive_coarse");
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      prof_collect();
+      const uint64_t n_surv = h.n_rec;
+      survivors = n_surv;
+      if (n_surv > rcap && (idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR)) {
+        two = false;  // too many survivors to hold: one exact pass instead
+      } else if (n_surv > rcap) {
+        // every passing record lies in a surviving super-bin, so f times the
+        // survivors bounds the total from above
+        *n_out = n_surv * f;
+        return GRIM_E_OVERFLOW;
+      } else {
+        int32_t* icand = reinterpret_cast<int32_t*>(ws + L.cand);
+        uint64_t* ioff = reinterpret_cast<uint64_t*>(ws + L.cand_off);
+        const RecordsView surv = sort_records(ra, rb, n_surv, read_bits + cbits, ws + L.hist, st);
+        expand_survivors(surv.keys, n_surv, cbits, f, n_reads, icand, ioff, st);
+        lists = icand;
+        lists_off = ioff;
+        n_lists = n_surv * f;
+        list_mode = true;
+      }
+      // restart the record and work counters for the next pass
+      CK(cudaMemsetAsync(ctl, 0, offsetof(Ctl, blocks), st));
+    }
+    if (two) launch_candidates(v, rv, lists, lists_off, ra, ctl, st, "candidates_refine");
+    else launch_exhaustive(v, rv, ra, bin_bits, h.max_d, ctl, st);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   prof_collect();
-  const int sc = status_to_code(h.status);
+  sc = status_to_code(h.status);
   if (sc != GRIM_OK) return sc;
   *n_out = h.n_rec;
   if (h.n_rec > cap) return GRIM_E_OVERFLOW;
   const uint32_t key_bits =
-      cand_mode ? bit_length(n_cand ? n_cand - 1 : 0)
-                : bin_bits + (n_reads > 1 ? bit_length((uint64_t)n_reads - 1) : 0);
-  sort_and_emit(ra, rb, h.n_rec, key_bits, ws + L.hist, cand_mode, bin_bits, cand, cand_off, n_reads,
-                out_read, out_bin, out_count, st);
+      list_mode ? bit_length(n_lists ? n_lists - 1 : 0) : bin_bits + read_bits;
+  sort_and_emit(ra, rb, h.n_rec, key_bits, ws + L.hist, list_mode, bin_bits, lists, lists_off,
+                n_reads, out_read, out_bin, out_count, st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   prof_collect();
@@ -358,6 +469,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   g_last_stats.n_records = h.n_rec;
   g_last_stats.pairs = cand_mode ? n_cand : (uint64_t)n_reads * v.num_bins;
   g_last_stats.tokens_executed = h.blocks * kBlockTokens;
+  g_last_stats.survivors = survivors;
   return GRIM_OK;
 }
 

@@ -120,9 +120,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
     for (uint64_t kb = c0; kb < c1; kb += CPW) {
       const uint64_t k = kb + slot;
       const bool valid = k < c1;
+      const uint32_t b = valid ? (uint32_t)__ldg(a.cand + k) : 0u;
       uint32_t sum = 0;
       if (valid) {
-        const uint32_t b = (uint32_t)__ldg(a.cand + k);
         uint32_t v[WL];
         load_words<WL>(a.ix.bm + (uint64_t)b * WPB + sub * WL, v);
 #pragma unroll
@@ -137,7 +137,10 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
       }
 #pragma unroll
       for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-      const bool pass = valid && sub == 0 && sum >= thr;
+      // bins past num_bins exist only as zero padding of the table (members
+      // of the last super-bin); they never pass
+      const bool real = valid && b < a.ix.num_bins;
+      const bool pass = real && sub == 0 && sum >= thr;
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
       if (bal) {
         unsigned long long base = 0;
@@ -156,7 +159,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
 }
 
 template <int WPB>
-void launch_t(const CandArgs& a, cudaStream_t st) {
+void launch_t(const CandArgs& a, cudaStream_t st, const char* name) {
   const uint32_t hist_words = a.ix.r4 >= 4 ? a.ix.r4 / 4 : 1;
   const size_t smem = (size_t)kWarps * hist_words * sizeof(uint32_t);
   int dev = 0, sms = 0, per_sm = 0;
@@ -168,22 +171,23 @@ void launch_t(const CandArgs& a, cudaStream_t st) {
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
-  ProfScope ps("candidates", st);
+  ProfScope ps(name, st);
   k_candidates<WPB><<<(unsigned)grid, kWarps * 32, smem, st>>>(a);
 }
 
 }  // namespace
 
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
-                       const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st) {
+                       const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
+                       const char* prof_name) {
   if (rv.n_reads == 0) return;
   CandArgs a{ix, rv, cand, cand_off, rec, ctl};
   switch (ix.wpb) {
-    case 1: launch_t<1>(a, st); break;
-    case 2: launch_t<2>(a, st); break;
-    case 8: launch_t<8>(a, st); break;
-    case 32: launch_t<32>(a, st); break;
-    case 128: launch_t<128>(a, st); break;
+    case 1: launch_t<1>(a, st, prof_name); break;
+    case 2: launch_t<2>(a, st, prof_name); break;
+    case 8: launch_t<8>(a, st, prof_name); break;
+    case 32: launch_t<32>(a, st, prof_name); break;
+    case 128: launch_t<128>(a, st, prof_name); break;
     default: break;  // q outside 2..6 is rejected by grim_build
   }
 }

@@ -125,6 +125,31 @@ __global__ void k_emit(const unsigned long long* __restrict__ keys,
   out_count[i] = counts[i];
 }
 
+// Survivors of the coarse pass (keys read << cbits | super-bin, sorted) become
+// candidate lists of the members of each surviving super-bin: candidates
+// f*i .. f*i+f-1 are bins f*s .. f*s+f-1, and read r's list starts at f times
+// the number of survivors of reads before r.
+__global__ void k_expand(const unsigned long long* __restrict__ keys, uint64_t n_surv,
+                         uint32_t cbits, uint32_t f, uint32_t n_reads, int32_t* __restrict__ cand,
+                         uint64_t* __restrict__ cand_off) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const unsigned long long mask = cbits >= 64 ? ~0ull : ((1ull << cbits) - 1ull);
+  if (i < n_surv) {
+    const uint32_t s = (uint32_t)(keys[i] & mask);
+    for (uint32_t k = 0; k < f; ++k) cand[f * i + k] = (int32_t)(f * s + k);
+  }
+  if (i <= n_reads) {
+    const unsigned long long target = (unsigned long long)i << cbits;
+    uint64_t lo = 0, hi = n_surv;  // first survivor with key >= target
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) / 2;
+      if (keys[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    cand_off[i] = f * lo;
+  }
+}
+
 }  // namespace
 
 uint64_t sort_workspace_bytes(uint64_t cap) {
@@ -132,11 +157,17 @@ uint64_t sort_workspace_bytes(uint64_t cap) {
   return 256ull * (nb ? nb : 1) * sizeof(uint32_t);
 }
 
-void sort_and_emit(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
-                   bool candidate_mode, uint32_t bin_bits, const int32_t* cand,
-                   const uint64_t* cand_off, uint32_t n_reads, uint32_t* out_read,
-                   uint32_t* out_bin, uint8_t* out_count, cudaStream_t st) {
-  if (n == 0) return;
+void expand_survivors(const unsigned long long* keys, uint64_t n_surv, uint32_t cbits, uint32_t f,
+                      uint32_t n_reads, int32_t* cand, uint64_t* cand_off, cudaStream_t st) {
+  const uint64_t n = n_surv > (uint64_t)n_reads + 1 ? n_surv : (uint64_t)n_reads + 1;
+  ProfScope ps("expand", st);
+  k_expand<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, n_surv, cbits, f, n_reads, cand,
+                                                       cand_off);
+}
+
+RecordsView sort_records(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
+                         cudaStream_t st) {
+  if (n == 0) return a;
   const uint32_t nb = (uint32_t)((n + kSortTile - 1) / kSortTile);
   uint32_t* h = static_cast<uint32_t*>(hist);
   RecordsView src = a, dst = b;
@@ -160,6 +191,15 @@ void sort_and_emit(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, 
     src = dst;
     dst = t;
   }
+  return src;
+}
+
+void sort_and_emit(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
+                   bool candidate_mode, uint32_t bin_bits, const int32_t* cand,
+                   const uint64_t* cand_off, uint32_t n_reads, uint32_t* out_read,
+                   uint32_t* out_bin, uint8_t* out_count, cudaStream_t st) {
+  if (n == 0) return;
+  const RecordsView src = sort_records(a, b, n, key_bits, hist, st);
   ProfScope ps("emit", st);
   k_emit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src.keys, src.counts, n, candidate_mode,
                                                       bin_bits, cand, cand_off, n_reads, out_read,

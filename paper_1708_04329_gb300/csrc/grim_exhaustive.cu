@@ -15,16 +15,23 @@
 //   fetches them for each token with one 16-byte shared load; a quarter warp
 //   reads one whole 128-byte row, so the four groups' loads of four rows are
 //   four conflict-free wavefronts.
+// * Each group copies the token row of the read it will take next into its
+//   own shared-memory slot with cp.async while it works on the current one,
+//   so the inner loop never waits on global memory.
 // * Instead of p separate counters, each lane keeps bit-sliced vertical
 //   counters: plane k of word w holds bit k of the counters of that word's 32
 //   bins.  Counted are MISSES (tokens absent from the bin), started at
-//   bias = 256 - (D'+1) with D' = min(q*e, L-q+1), so the 8-bit counter
+//   bias = 2^P - (D'+1) with D' = min(q*e, L-q+1), so the P-bit counter
 //   overflows exactly when misses > D', i.e. when sum < T = (L-q+1) - q*e.
 //   The overflow is kept in a sticky "dead" plane; a bin passes iff its dead
 //   bit is clear at the end, and then its sum is (L-q+1) - (counter - bias).
+//   P (5..8) is the smallest depth that holds the batch's largest D'.
 // * Tokens are added 16 at a time with a carry-save (Harley-Seal) tree of
-//   full adders (two 3-input LOP3s each), whose weight-16 carry ripples into
-//   the upper four planes: ~2.4 logic ops per token per 32 bins.
+//   full adders (two 3-input LOP3s each), whose weight-16 carry ripples
+//   through the P-4 upper planes: 2 logic ops per token per 32 bins at P = 5.
+//   The logic ops run on the integer pipe, which bounds this kernel; the
+//   token-to-address arithmetic is written as integer multiply-adds so that
+//   it runs on the FMA pipe instead.
 // * Early exit: after each 16-token block the group stops a read once every
 //   one of its 1024 bins is dead -- exact, since a dead bin can never pass.
 // * Groups advance independently (a finished group takes the range's next
@@ -36,7 +43,9 @@ namespace grim {
 namespace {
 
 constexpr int kThreads = 512;
+constexpr int kGroups = kThreads / 8;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint32_t kRowBytes = kTileWords * 4;  // one token's row of a tile
 
 #define LOP3(d, a, b, c, lut) \
   asm("lop3.b32 %0, %1, %2, %3, " #lut ";" : "=r"(d) : "r"(a), "r"(b), "r"(c))
@@ -54,102 +63,53 @@ __device__ __forceinline__ void fa_miss(uint32_t a, uint32_t b, uint32_t c, uint
   LOP3(k, a, b, c, 0x71);
 }
 
+// integer multiply-adds (FMA pipe); the multipliers come from kernel
+// arguments so they are not strength-reduced into shifts
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t imul_hi(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+template <int P>
 struct Counters {
-  // per word: s1 s2 s4 s8 (low planes), u[0..3] (weights 16..128), dead
-  uint32_t s1[4], s2[4], s4[4], s8[4], u0[4], u1[4], u2[4], u3[4], dead[4];
+  // per word: s1 s2 s4 s8 (weights 1..8), up[i] (weight 16 << i), dead
+  uint32_t s1[4], s2[4], s4[4], s8[4], up[P - 4][4], dead[4];
 
   __device__ __forceinline__ void init(uint32_t bias) {
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-      s1[w] = (bias & 1u) ? ~0u : 0u;
-      s2[w] = (bias & 2u) ? ~0u : 0u;
-      s4[w] = (bias & 4u) ? ~0u : 0u;
-      s8[w] = (bias & 8u) ? ~0u : 0u;
-      u0[w] = (bias & 16u) ? ~0u : 0u;
-      u1[w] = (bias & 32u) ? ~0u : 0u;
-      u2[w] = (bias & 64u) ? ~0u : 0u;
-      u3[w] = (bias & 128u) ? ~0u : 0u;
+      s1[w] = 0u - (bias & 1u);
+      s2[w] = 0u - ((bias >> 1) & 1u);
+      s4[w] = 0u - ((bias >> 2) & 1u);
+      s8[w] = 0u - ((bias >> 3) & 1u);
+#pragma unroll
+      for (int i = 0; i < P - 4; ++i) up[i][w] = 0u - ((bias >> (4 + i)) & 1u);
       dead[w] = 0u;
     }
   }
 
   // counter value of bin `bit` of word w
   __device__ __forceinline__ uint32_t value(int w, uint32_t bit) const {
-    return ((s1[w] >> bit) & 1u) | (((s2[w] >> bit) & 1u) << 1) | (((s4[w] >> bit) & 1u) << 2) |
-           (((s8[w] >> bit) & 1u) << 3) | (((u0[w] >> bit) & 1u) << 4) |
-           (((u1[w] >> bit) & 1u) << 5) | (((u2[w] >> bit) & 1u) << 6) |
-           (((u3[w] >> bit) & 1u) << 7);
+    uint32_t v = ((s1[w] >> bit) & 1u) | (((s2[w] >> bit) & 1u) << 1) |
+                 (((s4[w] >> bit) & 1u) << 2) | (((s8[w] >> bit) & 1u) << 3);
+#pragma unroll
+    for (int i = 0; i < P - 4; ++i) v |= ((up[i][w] >> bit) & 1u) << (4 + i);
+    return v;
   }
 };
-
-// Add the misses of one 16-token block: tw holds 16 table row indices
-// (uint16 pairs); lane_row points at this lane's 16 bytes of row 0.
-__device__ __forceinline__ void add_block(Counters& c, const uint32_t (&tw)[8],
-                                          const char* lane_row) {
-  // the 4 words (this lane's 128 bins) of token j's row
-#define ROW(j)                                                                          \
-  (*reinterpret_cast<const uint4*>(                                                     \
-      lane_row + (((j) & 1) ? (tw[(j) >> 1] >> 16) : (tw[(j) >> 1] & 0xFFFFu)) * 128u))
-  uint32_t t2a[4], t2b[4], t4a[4], t4b[4], t8a[4], t8b[4], t16[4];
-  {
-    uint4 x0 = ROW(0), x1 = ROW(1), x2 = ROW(2), x3 = ROW(3);
-    const uint32_t a0[4] = {x0.x, x0.y, x0.z, x0.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w};
-    const uint32_t a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      fa_miss(c.s1[w], a0[w], a1[w], c.s1[w], t2a[w]);
-      fa_miss(c.s1[w], a2[w], a3[w], c.s1[w], t2b[w]);
-      fa(c.s2[w], t2a[w], t2b[w], c.s2[w], t4a[w]);
-    }
-  }
-  {
-    uint4 x0 = ROW(4), x1 = ROW(5), x2 = ROW(6), x3 = ROW(7);
-    const uint32_t a0[4] = {x0.x, x0.y, x0.z, x0.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w};
-    const uint32_t a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      fa_miss(c.s1[w], a0[w], a1[w], c.s1[w], t2a[w]);
-      fa_miss(c.s1[w], a2[w], a3[w], c.s1[w], t2b[w]);
-      fa(c.s2[w], t2a[w], t2b[w], c.s2[w], t4b[w]);
-      fa(c.s4[w], t4a[w], t4b[w], c.s4[w], t8a[w]);
-    }
-  }
-  {
-    uint4 x0 = ROW(8), x1 = ROW(9), x2 = ROW(10), x3 = ROW(11);
-    const uint32_t a0[4] = {x0.x, x0.y, x0.z, x0.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w};
-    const uint32_t a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      fa_miss(c.s1[w], a0[w], a1[w], c.s1[w], t2a[w]);
-      fa_miss(c.s1[w], a2[w], a3[w], c.s1[w], t2b[w]);
-      fa(c.s2[w], t2a[w], t2b[w], c.s2[w], t4a[w]);
-    }
-  }
-  {
-    uint4 x0 = ROW(12), x1 = ROW(13), x2 = ROW(14), x3 = ROW(15);
-    const uint32_t a0[4] = {x0.x, x0.y, x0.z, x0.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w};
-    const uint32_t a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      fa_miss(c.s1[w], a0[w], a1[w], c.s1[w], t2a[w]);
-      fa_miss(c.s1[w], a2[w], a3[w], c.s1[w], t2b[w]);
-      fa(c.s2[w], t2a[w], t2b[w], c.s2[w], t4b[w]);
-      fa(c.s4[w], t4a[w], t4b[w], c.s4[w], t8b[w]);
-      fa(c.s8[w], t8a[w], t8b[w], c.s8[w], t16[w]);
-      // ripple the weight-16 carry through the upper planes; the carry out of
-      // weight 128 (counter >= 256: misses > D') sticks in `dead`
-      uint32_t k = t16[w], nk;
-      nk = c.u0[w] & k; c.u0[w] ^= k; k = nk;
-      nk = c.u1[w] & k; c.u1[w] ^= k; k = nk;
-      nk = c.u2[w] & k; c.u2[w] ^= k; k = nk;
-      uint32_t d;
-      LOP3(d, c.dead[w], c.u3[w], k, 0xF8);  // dead | (u3 & k)
-      c.u3[w] ^= k;
-      c.dead[w] = d;
-    }
-  }
-#undef ROW
-}
 
 struct ExhArgs {
   IndexView ix;
@@ -157,24 +117,89 @@ struct ExhArgs {
   RecordsView rec;
   uint32_t bin_bits;
   uint32_t n_ranges, reads_per_range, n_items;
+  uint32_t row_stride;  // bytes of one token row in a group slot (multiple of 16)
+  uint32_t slot_bytes;  // bytes of a group slot: two token rows
+  uint32_t c_row, c_hi, c_lo;  // 128, 65536, -65536: multipliers of the address math
   Ctl* ctl;
 };
 
+// Add the misses of one 16-token block.  tw holds 16 table row indices as
+// uint16 pairs; lane_base is the shared address of this lane's 16 bytes of
+// row 0.
+template <int P>
+__device__ __forceinline__ void add_block(Counters<P>& c, const uint32_t (&tw)[8],
+                                          uint32_t lane_base, const ExhArgs& a) {
+  uint32_t addr[16];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t hi = imul_hi(tw[j], a.c_hi);     // token 2j+1
+    const uint32_t lo = imad(hi, a.c_lo, tw[j]);    // token 2j
+    addr[2 * j] = imad(lo, a.c_row, lane_base);
+    addr[2 * j + 1] = imad(hi, a.c_row, lane_base);
+  }
+  uint32_t t2a[4], t2b[4], t4a[4], t4b[4], t8a[4], t8b[4], t16[4];
+#pragma unroll
+  for (int quad = 0; quad < 4; ++quad) {
+    const uint4 x0 = lds128(addr[4 * quad]), x1 = lds128(addr[4 * quad + 1]);
+    const uint4 x2 = lds128(addr[4 * quad + 2]), x3 = lds128(addr[4 * quad + 3]);
+    const uint32_t a0[4] = {x0.x, x0.y, x0.z, x0.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w};
+    const uint32_t a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      uint32_t* t4 = (quad & 1) ? t4b : t4a;
+      fa_miss(c.s1[w], a0[w], a1[w], c.s1[w], t2a[w]);
+      fa_miss(c.s1[w], a2[w], a3[w], c.s1[w], t2b[w]);
+      fa(c.s2[w], t2a[w], t2b[w], c.s2[w], t4[w]);
+      if (quad == 1) fa(c.s4[w], t4a[w], t4b[w], c.s4[w], t8a[w]);
+      if (quad == 3) {
+        fa(c.s4[w], t4a[w], t4b[w], c.s4[w], t8b[w]);
+        fa(c.s8[w], t8a[w], t8b[w], c.s8[w], t16[w]);
+        // ripple the weight-16 carry through the upper planes; the carry out
+        // of the top plane (counter >= 2^P: misses > D') sticks in `dead`
+        uint32_t k = t16[w];
+#pragma unroll
+        for (int i = 0; i < P - 5; ++i) {
+          const uint32_t nk = c.up[i][w] & k;
+          c.up[i][w] ^= k;
+          k = nk;
+        }
+        uint32_t d;
+        LOP3(d, c.dead[w], c.up[P - 5][w], k, 0xF8);  // dead | (top & k)
+        c.up[P - 5][w] ^= k;
+        c.dead[w] = d;
+      }
+    }
+  }
+}
+
+template <int P>
 __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
-  extern __shared__ __align__(16) uint32_t s_tile[];  // (r4 + 2) rows x 32 words
+  // [tile: (r4 + 2) rows x 128 B][64 group slots][16 padding tokens]
+  extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint32_t s_item, s_next;
   const uint32_t tid = threadIdx.x, lane = tid & 31, grp = lane >> 3, li = lane & 7;
   const uint32_t r4 = a.ix.r4;
   if (*(volatile uint32_t*)&a.ctl->status) return;  // set by the tokeniser before launch
 
+  uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem);
+  const uint32_t tile_bytes = (r4 + 2) * kRowBytes;
+  const uint32_t sh_base = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t slot = sh_base + tile_bytes + (tid >> 3) * a.slot_bytes;
+  const uint32_t pad_tokens = sh_base + tile_bytes + kGroups * a.slot_bytes;
   for (uint32_t i = tid; i < kTileWords; i += kThreads) {
     s_tile[rowInvalid(r4) * kTileWords + i] = 0u;
     s_tile[rowPad(r4) * kTileWords + i] = ~0u;
   }
-  const char* lane_row = reinterpret_cast<const char*>(s_tile) + li * 16u;
+  if (tid < 2) {  // 16 padding tokens = 32 bytes
+    const uint32_t pp = rowPad(r4) | (rowPad(r4) << 16);
+    asm volatile("st.shared.v4.u32 [%0], {%1,%1,%1,%1};" ::"r"(pad_tokens + tid * 16u), "r"(pp));
+  }
+  const uint32_t lane_base = sh_base + li * 16u;
+  const uint32_t row_chunks = a.rv.ts * 2u / 16u;  // 16-byte chunks of a token row
 
   for (;;) {
-    __syncthreads();  // previous item finished with the tile
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();  // previous item finished with the tile and the slots
     if (tid == 0) {
       s_item = atomicAdd(&a.ctl->item, 1u);
       s_next = 0;
@@ -189,17 +214,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
     // stage the tile: rows [0, r4), words [tile*32, tile*32+32)
     {
       const uint32_t* src = a.ix.tm + (uint64_t)tile * kTileWords;
-      const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(s_tile);
       for (uint32_t i = tid; i < r4 * 8u; i += kThreads) {
         const uint32_t row = i >> 3, chunk = i & 7u;
         const uint32_t* g = src + (uint64_t)row * a.ix.wpad + chunk * 4u;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + (row * 32u + chunk * 4u) * 4u),
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sh_base + row * kRowBytes +
+                                                                      chunk * 16u),
                      "l"(g));
       }
       asm volatile("cp.async.commit_group;");
-      asm volatile("cp.async.wait_all;" ::: "memory");
     }
-    __syncthreads();
 
     // which of this lane's 128 bins exist (only the last tile is ragged)
     uint32_t vmask[4];
@@ -210,47 +233,79 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
       vmask[w] = left >= 32 ? ~0u : ((1u << left) - 1u);
     }
 
-    // per-group state (identical in the group's 8 lanes)
-    uint32_t cur = kNone, blk = 0, nblk = 0, ntok = 0, bias = 0;
-    uint32_t executed = 0;  // blocks this group applied to real reads
+    // per-group state (identical in the group's 8 lanes); the group's slot
+    // holds two token rows: `buf` is the current read's, buf^1 the next's
+    uint32_t cur = kNone, nxt = kNone, nxt_meta = 0, buf = 1;
+    uint32_t blk = 0, nblk = 0, ntok = 0, bias = 0, executed = 0;
     bool fin = false;
-    const uint16_t* tk = a.rv.tokens + (uint64_t)r0 * a.rv.ts;  // any in-bounds block
-    Counters c;
+    Counters<P> c;
     c.init(0);
 
+    // take the first read and start copying its tokens
+    {
+      uint32_t k = 0;
+      if (li == 0) k = atomicAdd(&s_next, 1u);
+      k = __shfl_sync(0xFFFFFFFFu, k, grp * 8);
+      if (k < nr) {
+        nxt = r0 + k;
+        nxt_meta = __ldg(a.rv.meta + nxt);
+        const char* src = reinterpret_cast<const char*>(a.rv.tokens + (uint64_t)nxt * a.rv.ts);
+        for (uint32_t ch = li; ch < row_chunks; ch += 8)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(slot + ch * 16u),
+                       "l"(src + ch * 16u));
+      }
+      asm volatile("cp.async.commit_group;");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();  // tile staged
+
     for (;;) {
-      // (1) groups without a read take the range's next one
+      // (1) groups without a read switch to the one whose tokens were copied
+      //     ahead, and start copying the read after it
       const bool need = !fin && cur == kNone;
       if (__any_sync(0xFFFFFFFFu, need)) {
-        uint32_t k = 0;
-        if (need && li == 0) k = atomicAdd(&s_next, 1u);
-        k = __shfl_sync(0xFFFFFFFFu, k, grp * 8);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
         if (need) {
-          if (k >= nr) {
+          if (nxt == kNone) {
             fin = true;
-            blk = 0;  // keep re-reading an in-bounds block
           } else {
-            cur = r0 + k;
-            const uint32_t m = a.rv.meta[cur];
-            ntok = m & 0xFFu;
-            const uint32_t d = (m >> 8) & 0xFFu;
-            bias = 256u - (d + 1u);
+            cur = nxt;
+            buf ^= 1u;
+            ntok = nxt_meta & 0xFFu;
+            const uint32_t d = (nxt_meta >> 8) & 0xFFu;
+            bias = (1u << P) - (d + 1u);
             nblk = (ntok + kBlockTokens - 1) / kBlockTokens;
             blk = 0;
-            tk = a.rv.tokens + (uint64_t)cur * a.rv.ts;
             c.init(bias);
           }
         }
+        const bool take = need && !fin;
+        uint32_t k = 0;
+        if (take && li == 0) k = atomicAdd(&s_next, 1u);
+        k = __shfl_sync(0xFFFFFFFFu, k, grp * 8);
+        if (take) {
+          nxt = k < nr ? r0 + k : kNone;
+          if (nxt != kNone) {
+            nxt_meta = __ldg(a.rv.meta + nxt);
+            const char* src = reinterpret_cast<const char*>(a.rv.tokens + (uint64_t)nxt * a.rv.ts);
+            const uint32_t dst = slot + (buf ^ 1u) * a.row_stride;
+            for (uint32_t ch = li; ch < row_chunks; ch += 8)
+              asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst + ch * 16u),
+                           "l"(src + ch * 16u));
+          }
+        }
+        asm volatile("cp.async.commit_group;");
       }
       if (__all_sync(0xFFFFFFFFu, fin)) break;
 
-      // (2) one 16-token block for all four groups (finished groups repeat
-      //     an in-bounds block; their results are ignored)
+      // (2) one 16-token block for all four groups (finished groups apply
+      //     padding tokens; their results are ignored)
       {
-        const uint4* tp = reinterpret_cast<const uint4*>(tk + blk * kBlockTokens);
-        const uint4 t0 = __ldg(tp), t1 = __ldg(tp + 1);
+        const uint32_t tp = fin ? pad_tokens : slot + buf * a.row_stride + blk * 32u;
+        const uint4 t0 = lds128(tp), t1 = lds128(tp + 16u);
         const uint32_t tw[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-        add_block(c, tw, lane_row);
+        add_block<P>(c, tw, lane_base, a);
       }
       if (!fin) {
         ++blk;
@@ -261,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
       const uint32_t all_dead = c.dead[0] & c.dead[1] & c.dead[2] & c.dead[3];
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, all_dead == ~0u);
       const bool gdead = ((bal >> (grp * 8)) & 0xFFu) == 0xFFu;
-      const bool done = !fin && cur != kNone && (gdead || blk >= nblk);
+      const bool done = !fin && (gdead || blk >= nblk);
       const bool emit = done && !gdead;
       if (__any_sync(0xFFFFFFFFu, emit)) {
         uint32_t pm[4], cnt = 0;
@@ -306,10 +361,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
   }
 }
 
+template <int P>
+void launch_p(const ExhArgs& a, size_t smem, uint32_t grid, cudaStream_t st, const char* name) {
+  cudaFuncSetAttribute(k_exhaustive<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ProfScope ps(name, st);
+  k_exhaustive<P><<<grid, kThreads, smem, st>>>(a);
+}
+
 }  // namespace
 
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
-                       Ctl* ctl, cudaStream_t st) {
+                       uint32_t max_d, Ctl* ctl, cudaStream_t st, const char* prof_name) {
   if (rv.n_reads == 0) return;
   const uint32_t n_tiles = (uint32_t)(ix.num_bins_pad / kTileBins);
   int dev = 0, sms = 0;
@@ -323,13 +385,30 @@ void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec
   if (n_ranges < 1) n_ranges = 1;
   const uint32_t per = (rv.n_reads + n_ranges - 1) / n_ranges;
   n_ranges = (rv.n_reads + per - 1) / per;
-  ExhArgs a{ix, rv, rec, bin_bits, n_ranges, per, n_tiles * n_ranges, ctl};
-  const size_t smem = (size_t)(ix.r4 + 2) * kTileWords * sizeof(uint32_t);
-  cudaFuncSetAttribute(k_exhaustive, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  ExhArgs a{};
+  a.ix = ix;
+  a.rv = rv;
+  a.rec = rec;
+  a.bin_bits = bin_bits;
+  a.n_ranges = n_ranges;
+  a.reads_per_range = per;
+  a.n_items = n_tiles * n_ranges;
+  a.row_stride = rv.ts * 2u;
+  // slots of consecutive groups start 32 bytes apart modulo 128, so the four
+  // groups of a warp mostly read their tokens from different banks
+  a.slot_bytes = (2u * a.row_stride + 127u) / 128u * 128u + 32u;
+  a.c_row = kRowBytes;
+  a.c_hi = 65536u;
+  a.c_lo = 0u - 65536u;
+  a.ctl = ctl;
+  const size_t smem = (size_t)(ix.r4 + 2) * kRowBytes + (size_t)kGroups * a.slot_bytes + 32;
   uint32_t grid = (uint32_t)sms;
   if (grid > a.n_items) grid = a.n_items;
-  ProfScope ps("exhaustive", st);
-  k_exhaustive<<<grid, kThreads, smem, st>>>(a);
+  // the counters need 2^P > D' (D' <= 255)
+  if (max_d < 32) launch_p<5>(a, smem, grid, st, prof_name);
+  else if (max_d < 64) launch_p<6>(a, smem, grid, st, prof_name);
+  else if (max_d < 128) launch_p<7>(a, smem, grid, st, prof_name);
+  else launch_p<8>(a, smem, grid, st, prof_name);
 }
 
 }  // namespace grim

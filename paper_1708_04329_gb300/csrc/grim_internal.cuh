@@ -24,7 +24,8 @@ struct Ctl {
   uint32_t status;            // kStatus* bits
   uint32_t item;              // work-item counter of the persistent filter kernels
   unsigned long long blocks;  // 16-token blocks applied to 1024-bin tiles (all-bins mode)
-  uint32_t pad[58];
+  uint32_t max_d;             // largest miss budget D' = min(q*e, L-q+1) of the batch
+  uint32_t pad[57];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte slot");
 
@@ -77,14 +78,21 @@ void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t*
 void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
                              uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st);
 
+// max_d: the batch's largest miss budget (sizes the bit-sliced counters)
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
-                       Ctl* ctl, cudaStream_t st);
+                       uint32_t max_d, Ctl* ctl, cudaStream_t st,
+                       const char* prof_name = "exhaustive");
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
-                       const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st);
+                       const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
+                       const char* prof_name = "candidates");
 
 // Radix sort of n (key, count) records by the low key_bits bits of the key,
 // followed by the split into the caller's (read, bin, count) arrays.
 uint64_t sort_workspace_bytes(uint64_t cap);
+RecordsView sort_records(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
+                         cudaStream_t st);  // returns whichever of a, b holds the sorted keys
+void expand_survivors(const unsigned long long* keys, uint64_t n_surv, uint32_t cbits, uint32_t f,
+                      uint32_t n_reads, int32_t* cand, uint64_t* cand_off, cudaStream_t st);
 void sort_and_emit(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
                    bool candidate_mode, uint32_t bin_bits, const int32_t* cand,
                    const uint64_t* cand_off, uint32_t n_reads, uint32_t* out_read,

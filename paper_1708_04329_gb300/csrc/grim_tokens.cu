@@ -50,6 +50,8 @@ __global__ void k_tokenise(const char* __restrict__ reads, const uint64_t* __res
     uint32_t d = q * (uint32_t)e[r];
     if (d > ntok) d = ntok;
     meta[r] = ntok | (d << 8);
+    // most batches share one budget: skip the atomic once the max is reached
+    if (d > *reinterpret_cast<volatile uint32_t*>(&ctl->max_d)) atomicMax(&ctl->max_d, d);
   }
 }
 

@@ -31,6 +31,9 @@ GRIM_E_UNSUPPORTED = -11
 GRIM_LAYOUT_TOKEN_MAJOR = 1
 GRIM_LAYOUT_BIN_MAJOR = 2
 GRIM_LAYOUT_BOTH = 3
+GRIM_LAYOUT_COARSE = 4
+GRIM_LAYOUT_ALL = 7
+GRIM_COARSE_FACTOR = 2
 
 #: every symbol include/grim.h declares
 EXPORTS = (
@@ -56,12 +59,14 @@ class _Desc(C.Structure):
                 ("max_read_len", C.c_uint32), ("layouts", C.c_uint32),
                 ("words_per_bin", C.c_uint32), ("token_major", C.c_void_p),
                 ("bin_major", C.c_void_p), ("token_major_bytes", C.c_uint64),
-                ("bin_major_bytes", C.c_uint64)]
+                ("bin_major_bytes", C.c_uint64), ("coarse_token_major", C.c_void_p),
+                ("num_coarse", C.c_uint64), ("num_coarse_pad", C.c_uint64),
+                ("coarse_token_major_bytes", C.c_uint64), ("coarse_factor", C.c_uint32)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("n_reads", C.c_uint64), ("n_records", C.c_uint64), ("pairs", C.c_uint64),
-                ("tokens_executed", C.c_uint64)]
+                ("tokens_executed", C.c_uint64), ("survivors", C.c_uint64)]
 
 
 class _KTime(C.Structure):
@@ -191,6 +196,11 @@ class IndexDesc:
     bin_major_ptr: int
     token_major_bytes: int
     bin_major_bytes: int
+    coarse_token_major_ptr: int = 0
+    num_coarse: int = 0
+    num_coarse_pad: int = 0
+    coarse_token_major_bytes: int = 0
+    coarse_factor: int = 0
 
 
 class GrimIndex:
@@ -232,6 +242,16 @@ class GrimIndex:
         view = _CudaArray(d.token_major_ptr, shape, "<i4", self)
         return torch.as_tensor(view, device="cuda")
 
+    def coarse_token_major(self):
+        """Zero-copy int32-typed CUDA tensor [4^q, num_coarse_pad/32] of the
+        super-bin table's words (None if absent)."""
+        d = self.desc
+        if not d.coarse_token_major_ptr:
+            return None
+        torch = _torch()
+        view = _CudaArray(d.coarse_token_major_ptr, (4 ** d.q, d.num_coarse_pad // 32), "<i4", self)
+        return torch.as_tensor(view, device="cuda")
+
     def bin_major(self):
         """Zero-copy CUDA tensor [num_bins, words_per_bin] of the table's uint32
         words, typed int32.  None if the index has no bin-major table."""
@@ -243,7 +263,7 @@ class GrimIndex:
         return torch.as_tensor(view, device="cuda")
 
 
-def grim_build(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_BOTH,
+def grim_build(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
                stream=None) -> GrimIndex:
     """grim_build: ``ref`` is a uint8 CUDA tensor of ASCII bases."""
     h = C.c_void_p()
@@ -254,7 +274,7 @@ def grim_build(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOU
     return GrimIndex(h.value)
 
 
-def grim_build_host(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_BOTH,
+def grim_build_host(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
                     stream=None) -> GrimIndex:
     """grim_build_host: ``ref`` is host memory (numpy uint8 / CPU tensor)."""
     p, keep = _hptr(ref, "ref", np.uint8)
@@ -273,7 +293,8 @@ def grim_index_info(index: GrimIndex) -> IndexDesc:
         raise GrimError(rc, "grim_index_info")
     return IndexDesc(d.ref_len, d.num_bins, d.num_bins_pad, d.B, d.q, d.ext, d.max_read_len,
                      d.layouts, d.words_per_bin, d.token_major or 0, d.bin_major or 0,
-                     d.token_major_bytes, d.bin_major_bytes)
+                     d.token_major_bytes, d.bin_major_bytes, d.coarse_token_major or 0,
+                     d.num_coarse, d.num_coarse_pad, d.coarse_token_major_bytes, d.coarse_factor)
 
 
 def grim_free(index: GrimIndex) -> None:

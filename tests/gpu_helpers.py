@@ -14,7 +14,7 @@ def dev_reads(rs):
                 e=torch.from_numpy(np.ascontiguousarray(rs.e, np.uint16).view(np.int16)).cuda())
 
 
-def build(genome: np.ndarray, B: int, q: int, mrl: int, layouts: int = 3):
+def build(genome: np.ndarray, B: int, q: int, mrl: int, layouts: int = 7):
     import torch
 
     from paper_1708_04329_gb300 import grim

@@ -33,15 +33,23 @@ def _gpu_tables(idx, q):
             None if bm is None else bm.cpu().numpy().view(np.uint32))
 
 
-def _check_tables(ref: np.ndarray, B: int, q: int, mrl: int):
-    idx = build(ref, B, q, mrl)
+def _check_tables(ref: np.ndarray, B: int, q: int, mrl: int, layouts: int = 7):
+    idx = build(ref, B, q, mrl, layouts)
     tm, bm = _gpu_tables(idx, q)
     oix = oracle.bin_vectors(ref, B, q, mrl)
     vb = oracle.vector_bytes(q)
-    got = bm.view(np.uint8).reshape(oix.num_bins, -1)
-    assert np.array_equal(got[:, :vb], oix.vecs)
-    assert not got[:, vb:].any()
-    assert np.array_equal(tm, oracle.token_major(oix))
+    if bm is not None:
+        got = bm.view(np.uint8).reshape(oix.num_bins, -1)
+        assert np.array_equal(got[:, :vb], oix.vecs)
+        assert not got[:, vb:].any()
+    if tm is not None:
+        assert np.array_equal(tm, oracle.token_major(oix))
+    ctm = idx.coarse_token_major()
+    if ctm is not None:
+        # super-bins of 2 bins: the oracle's vectors with core 2B, same extension
+        coarse = oracle.bin_vectors(ref, 2 * B, q, mrl)
+        assert np.array_equal(ctm.cpu().numpy().view(np.uint32), oracle.token_major(coarse))
+        assert idx.desc.num_coarse == coarse.num_bins
     d = idx.desc
     assert d.num_bins == oix.num_bins and d.num_bins_pad % 1024 == 0
     return idx, oix
@@ -100,19 +108,22 @@ def test_handworked_fixture_gpu():
     assert list(zip(r.tolist(), b.tolist(), c.tolist())) == fx["pass"]
 
 
+@pytest.mark.parametrize("layouts", [1, 6, 7])
 @pytest.mark.parametrize("seed", range(8))
-def test_random_all_bins(seed):
+def test_random_all_bins(seed, layouts):
     """Several 1024-bin tiles plus a ragged one, mixed read lengths, non-bases,
-    per-read e including T <= 0."""
+    per-read e including T <= 0; one exact pass over the token-major table
+    (layouts 1), coarse-then-exact (6), or whichever the batch suits (7)."""
     rng = np.random.default_rng(500 + seed)
     q = int(rng.choice([2, 3, 4, 5]))
     B = int(rng.integers(5, 40))
     mrl = int(rng.integers(max(q, 20), 120))
     n = int(rng.integers(30_000, 90_000))
     ref, reads, e = random_case(rng, q, n, B, mrl, 300)
-    e = [int(x) if rng.random() < 0.9 else 40 for x in e]
+    if seed % 2:  # half the cases with some T <= 0 reads
+        e = [int(x) if rng.random() < 0.9 else 40 for x in e]
     rs = Reads(reads, e)
-    idx, oix = _check_tables(_np(ref), B, q, mrl)
+    idx, oix = _check_tables(_np(ref), B, q, mrl, layouts)
     assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
 
 
@@ -243,6 +254,14 @@ def test_overflow_reports_total_and_count_only():
         assert ei.value.code == grim.GRIM_E_OVERFLOW and ei.value.n_out == n
     # the binding's retry returns the full list
     assert_same(gpu_filter(idx, rs, cap=1), want)
+    # coarse-then-exact without a token-major table: an overflow of the
+    # survivors reports an upper bound, and the retry with it succeeds
+    cto = build(g, 100, 5, 100, layouts=6)
+    out = tuple(torch.empty(3, dtype=dt, device="cuda") for dt in (torch.int32, torch.int32, torch.uint8))
+    with pytest.raises(grim.GrimError) as ei:
+        grim.grim_filter(cto, **dev_reads(rs), out=out)
+    assert ei.value.code == grim.GRIM_E_OVERFLOW and ei.value.n_out >= n
+    assert_same(gpu_filter(cto, rs, cap=3), want)
 
 
 def test_workspace_reuse_is_clean():
