@@ -16,6 +16,7 @@ struct grim_index {
   uint32_t* tm;
   uint32_t* bm;
   uint32_t* ctm;
+  uint32_t* presence;
 };
 
 namespace grim {
@@ -230,6 +231,7 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
     cudaFree(ix->tm);
     cudaFree(ix->bm);
     cudaFree(ix->ctm);
+    cudaFree(ix->presence);
     delete ix;
     return code;
   };
@@ -246,11 +248,17 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
     e = cudaMalloc(&ix->ctm, (uint64_t)cv.r4 * cv.wpad * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(cuda_fail(e));
   }
+  if (layouts & (GRIM_LAYOUT_COARSE | GRIM_LAYOUT_TOKEN_MAJOR)) {
+    e = cudaMalloc(&ix->presence, (uint64_t)v.r4 * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(cuda_fail(e));
+  }
   v.tm = ix->tm;
   v.bm = ix->bm;
+  v.presence = ix->presence;
   ix->v = v;
   cv.tm = ix->ctm;
   cv.bm = nullptr;
+  cv.presence = ix->presence;
   ix->cv = cv;
 
   // packed reference (one spare word at the end of each array for the
@@ -269,6 +277,9 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
   launch_pack_ref(ref, len, codes, invalid, st);
   if (ix->tm) launch_build_token_major(codes, invalid, v, ix->tm, st);
   if (ix->ctm) launch_build_token_major(codes, invalid, cv, ix->ctm, st);
+  // token presence from the table the all-bins filter sweeps first
+  if (ix->ctm) launch_row_popcount(ix->ctm, cv.r4, cv.wpad, ix->presence, st);
+  else if (ix->tm) launch_row_popcount(ix->tm, v.r4, v.wpad, ix->presence, st);
   if (ix->bm) {
     if (bm_bins > v.num_bins)
       cudaMemsetAsync(ix->bm + v.num_bins * v.wpb, 0,
@@ -340,6 +351,7 @@ void grim_free(grim_index* idx) {
   cudaFree(idx->tm);
   cudaFree(idx->bm);
   cudaFree(idx->ctm);
+  cudaFree(idx->presence);
   delete idx;
 }
 

@@ -132,7 +132,31 @@ __global__ void __launch_bounds__(512) k_build_token_major(const uint32_t* __res
   }
 }
 
+// One CTA per token row: the number of set bits, i.e. how many (super-)bins
+// hold the token.
+__global__ void k_row_popcount(const uint32_t* __restrict__ tm, uint64_t words,
+                               uint32_t* __restrict__ presence) {
+  __shared__ unsigned long long part[32];
+  const uint32_t* row = tm + (uint64_t)blockIdx.x * words;
+  unsigned long long c = 0;
+  for (uint64_t i = threadIdx.x; i < words; i += blockDim.x) c += __popc(__ldg(row + i));
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    c = threadIdx.x < blockDim.x / 32 ? part[threadIdx.x] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (threadIdx.x == 0) presence[blockIdx.x] = (uint32_t)(c > 0xFFFFFFFFull ? 0xFFFFFFFFull : c);
+  }
+}
+
 }  // namespace
+
+void launch_row_popcount(const uint32_t* tm, uint32_t rows, uint64_t words_per_row,
+                         uint32_t* presence, cudaStream_t st) {
+  ProfScope ps("row_popcount", st);
+  k_row_popcount<<<rows, 512, 0, st>>>(tm, words_per_row, presence);
+}
 
 void launch_pack_ref(const char* ref, uint64_t n, uint32_t* codes, uint32_t* invalid,
                      cudaStream_t st) {

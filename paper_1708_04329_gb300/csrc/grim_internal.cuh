@@ -46,6 +46,10 @@ struct IndexView {
   uint32_t B, q, ext, max_read_len, r4, wpb;
   const uint32_t* tm;  // token-major [r4][wpad]
   const uint32_t* bm;  // bin-major [num_bins][wpb]
+  // [r4] number of (super-)bins holding each token, or null; the tokeniser
+  // orders each read's tokens by it so that the all-bins kernels apply the
+  // rarest tokens first and every bin of a tile fails as early as possible
+  const uint32_t* presence;
 };
 
 // Reads after tokenising: tokens[r * ts + j], meta[r] = ntok | D' << 8 where
@@ -71,6 +75,9 @@ void launch_build_bin_major(const uint32_t* codes, const uint32_t* invalid, cons
                             uint32_t* bm, cudaStream_t st);
 void launch_build_token_major(const uint32_t* codes, const uint32_t* invalid, const IndexView& ix,
                               uint32_t* tm, cudaStream_t st);
+// presence[t] = popcount of row t of a token-major table
+void launch_row_popcount(const uint32_t* tm, uint32_t rows, uint64_t words_per_row,
+                         uint32_t* presence, cudaStream_t st);
 
 void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t* lens,
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,

@@ -6,20 +6,29 @@
 namespace grim {
 namespace {
 
-// One warp per read.  tokens[r*ts + j] is the table row of token j:
-// its value for a clean q-gram, rowInvalid for one holding a non-base (it
-// still counts among the L-q+1 tokens and can never be found), rowPad past
-// the last token.  meta[r] = ntok | D' << 8 with D' = min(q*e, ntok): a bin
-// passes iff at most D' of the read's tokens are missing from it, which is
-// sum >= (L-q+1) - q*e.
-__global__ void k_tokenise(const char* __restrict__ reads, const uint64_t* __restrict__ offsets,
-                           const uint32_t* __restrict__ lens, const uint16_t* __restrict__ e,
-                           uint32_t n_reads, uint32_t q, uint32_t max_read_len, uint32_t r4,
-                           uint32_t ts, uint16_t* __restrict__ tokens, uint32_t* __restrict__ meta,
-                           Ctl* ctl) {
-  const uint32_t lane = threadIdx.x & 31;
+constexpr int kTokWarps = 8;
+constexpr uint32_t kMaxStride = 256;  // token stride: <= 255 tokens rounded up to 16
+
+// One warp per read.  The read's tokens (row indices of the table: the token
+// value for a clean q-gram, rowInvalid for one holding a non-base -- it still
+// counts among the L-q+1 tokens and can never be found -- and rowPad after
+// the last token) are written to tokens[r*ts ...].  With a presence table
+// they are written rarest first -- q-grams with a non-base, which every bin
+// misses, then ascending number of (super-)bins holding the token, ties by
+// position -- so that the all-bins kernels see misses as early as possible;
+// a sum does not depend on the order.  meta[r] = ntok | D' << 8 with
+// D' = min(q*e, ntok): a bin passes iff at most D' of the read's tokens are
+// missing from it, which is sum >= (L-q+1) - q*e.
+__global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
+    const char* __restrict__ reads, const uint64_t* __restrict__ offsets,
+    const uint32_t* __restrict__ lens, const uint16_t* __restrict__ e, uint32_t n_reads, uint32_t q,
+    uint32_t max_read_len, uint32_t r4, uint32_t ts, const uint32_t* __restrict__ presence,
+    uint16_t* __restrict__ tokens, uint32_t* __restrict__ meta, Ctl* ctl) {
+  __shared__ unsigned long long s_key[kTokWarps][kMaxStride];
+  __shared__ uint16_t s_row[kTokWarps][kMaxStride];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  if (r >= n_reads) return;
+  if (r >= n_reads) return;  // whole warps only: the warp syncs below stay uniform
   const uint32_t L = lens[r];
   const uint64_t off = offsets[r];
   uint16_t* out = tokens + r * ts;
@@ -32,20 +41,27 @@ __global__ void k_tokenise(const char* __restrict__ reads, const uint64_t* __res
     bad = true;
   }
   const uint32_t ntok = bad ? 0 : L - q + 1;
-  for (uint32_t j = lane; j < ts; j += 32) {
-    uint32_t row = rowPad(r4);
-    if (j < ntok) {
-      uint32_t v = 0;
-      bool clean = true;
-      for (uint32_t i = 0; i < q; ++i) {
-        uint32_t u = (uint8_t)reads[off + j + i] & 0xDFu;  // fold lowercase letters
-        clean &= (u == 0x41u) | (u == 0x43u) | (u == 0x47u) | (u == 0x54u);
-        v = (v << 2) | (((u >> 1) ^ (u >> 2)) & 3u);  // A0 C1 G2 T3
-      }
-      row = clean ? v : rowInvalid(r4);
+  for (uint32_t j = lane; j < ntok; j += 32) {
+    uint32_t v = 0;
+    bool clean = true;
+    for (uint32_t i = 0; i < q; ++i) {
+      const uint32_t u = (uint8_t)reads[off + j + i] & 0xDFu;  // fold lowercase letters
+      clean &= (u == 0x41u) | (u == 0x43u) | (u == 0x47u) | (u == 0x54u);
+      v = (v << 2) | (((u >> 1) ^ (u >> 2)) & 3u);  // A0 C1 G2 T3
     }
-    out[j] = (uint16_t)row;
+    const uint32_t row = clean ? v : rowInvalid(r4);
+    s_row[warp][j] = (uint16_t)row;
+    const unsigned long long rare = !presence ? 0ull : clean ? (unsigned long long)presence[row] + 1 : 0ull;
+    s_key[warp][j] = (rare << 8) | j;
   }
+  __syncwarp();
+  for (uint32_t j = lane; j < ntok; j += 32) {
+    const unsigned long long mine = s_key[warp][j];
+    uint32_t rank = 0;
+    for (uint32_t i = 0; i < ntok; ++i) rank += s_key[warp][i] < mine;
+    out[rank] = s_row[warp][j];
+  }
+  for (uint32_t j = ntok + lane; j < ts; j += 32) out[j] = (uint16_t)rowPad(r4);
   if (lane == 0) {
     uint32_t d = q * (uint32_t)e[r];
     if (d > ntok) d = ntok;
@@ -75,11 +91,12 @@ void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t*
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
                      uint32_t* meta, Ctl* ctl, cudaStream_t st) {
   if (rv.n_reads == 0) return;
-  const uint32_t threads = 256;
+  const uint32_t threads = kTokWarps * 32;
   uint64_t grid = ((uint64_t)rv.n_reads * 32 + threads - 1) / threads;
   ProfScope ps("tokenise", st);
   k_tokenise<<<(unsigned)grid, threads, 0, st>>>(reads, offsets, lens, e, rv.n_reads, ix.q,
-                                                 ix.max_read_len, ix.r4, rv.ts, tokens, meta, ctl);
+                                                 ix.max_read_len, ix.r4, rv.ts, ix.presence, tokens,
+                                                 meta, ctl);
 }
 
 void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
