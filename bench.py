@@ -52,6 +52,11 @@ def parse_args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--workload", default="human", choices=["human", "finer"],
+                   help="human: B=200, q=5, L=100, e=5 (the headline); finer: B=100, q=6, "
+                        "L=150, e=7 on the same genome")
+    p.add_argument("--coarse-factor", type=int, default=0,
+                   help="bins per super-bin of the coarse table (0: the library's choice)")
     p.add_argument("--genome", type=int, default=3_100_000_000, help="reference length (bases)")
     p.add_argument("--reads", type=int, default=1_000_000, help="reads per rank")
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -82,28 +87,41 @@ def workload(args, rank: int):
 
     t0 = time.perf_counter()
     g = synth.human_genome(args.genome)
-    w = synth.human_exhaustive(n_reads=args.reads, g=g) if rank == 0 else None
-    if w is None:  # other ranks: their own reads (weak scaling)
-        rs = synth.reads(g, args.reads, seed=3 + 7919 * rank, lengths=(100,), e=5, max_edits=5)
-        w = dict(name="human_exhaustive", genome=g, B=200, q=5, max_read_len=100, reads=rs)
+    if args.workload == "finer":
+        w = synth.finer_index(n_reads=args.reads, g=g)
+        if rank:  # other ranks: their own reads (weak scaling)
+            w["reads"] = synth.reads(g, args.reads, seed=5 + 7919 * rank, lengths=(150,), e=7,
+                                     max_edits=7)
+    else:
+        w = synth.human_exhaustive(n_reads=args.reads, g=g)
+        if rank:
+            w["reads"] = synth.reads(g, args.reads, seed=3 + 7919 * rank, lengths=(100,), e=5,
+                                     max_edits=5)
     nb = (len(g) + w["B"] - 1) // w["B"]
-    off, cand = synth.candidates((w["reads"].true_pos // w["B"]).astype(np.int32), nb, seed=4 + rank)
+    off, cand = synth.candidates((w["reads"].true_pos // w["B"]).astype(np.int32), nb,
+                                 seed=(5 if args.workload == "finer" else 4) + rank)
     w["cand_off"], w["cand"] = off, cand
+    w["read_len"] = int(w["reads"].lens[0])
+    w["e"] = int(w["reads"].e[0])
     w["gen_s"] = time.perf_counter() - t0
     return w
 
 
 def config_of(args, w):
     nb = (len(w["genome"]) + w["B"] - 1) // w["B"]
+    table_gb = nb * 4 ** w["q"] / 8 / 1e9
+    kind = "human-scale exhaustive" if args.workload == "human" else "finer index"
     return {
-        "workload": (f"human-scale exhaustive: {len(w['genome']) / 1e9:.1f} Gbp synthetic genome "
+        "workload": (f"{kind}: {len(w['genome']) / 1e9:.1f} Gbp synthetic genome "
                      f"(41% GC, ~50% copies of 500 repeat families), B={w['B']}, q={w['q']}, "
-                     f"{nb} bins, {w['reads'].n} reads L=100 e=5 against every bin; step = "
-                     f"grim_build (bin-major, token-major and coarse tables) + all-bins grim_filter + candidate-list "
-                     f"grim_filter ({len(w['cand'])} candidates)"),
+                     f"{nb} bins, {w['reads'].n} reads L={w['read_len']} e={w['e']} against every "
+                     f"bin; step = grim_build (bin-major, token-major and coarse tables) + all-bins "
+                     f"grim_filter + candidate-list grim_filter ({len(w['cand'])} candidates)"),
         "genome_bases": len(w["genome"]), "bins": nb, "reads_per_gpu": w["reads"].n,
-        "candidates_per_gpu": int(len(w["cand"])), "B": w["B"], "q": w["q"], "e": 5,
-        "read_len": 100, "l2": "inputs larger than L2 (1.98 GB token-major table, 3.1 GB reference)",
+        "candidates_per_gpu": int(len(w["cand"])), "B": w["B"], "q": w["q"], "e": w["e"],
+        "read_len": w["read_len"],
+        "l2": f"inputs larger than L2 ({table_gb:.2f} GB token-major table, "
+              f"{len(w['genome']) / 1e9:.1f} GB reference)",
     }
 
 
@@ -204,7 +222,7 @@ def run_native(args, rank, world, local):
 
     def step():
         evs[0].record(st)
-        idx = grim.grim_build(ref, B, q, mrl, grim.GRIM_LAYOUT_ALL, stream=st)
+        idx = grim.grim_build_ex(ref, B, q, mrl, grim.GRIM_LAYOUT_ALL, args.coarse_factor, stream=st)
         evs[1].record(st)
         a = grim.grim_filter(idx, **dev, out=outs[0], workspace=ws, stream=st)
         evs[2].record(st)
@@ -253,7 +271,7 @@ def run_native(args, rank, world, local):
     desc = counts.pop("desc")
     stats = counts.pop("stats")
     nb = desc.num_bins
-    ntok = 100 - q + 1
+    ntok = w["read_len"] - q + 1
     dom = max((k for k in prof if k.startswith("exhaustive")), key=lambda k: prof[k][1])
     k_launch, k_ms = prof[dom]
     per_launch_ms = k_ms / max(k_launch, 1)
@@ -269,7 +287,7 @@ def run_native(args, rank, world, local):
     # shared-memory datapath: 128 B/clk/SM = 1024 bit tests/clk/SM
     peak_tbit = n_sm * 1024 * sm_max * 1e6 / 1e12
     achieved_tbit = kernel_bit_tests / (per_launch_ms / 1e3) / 1e12
-    executed = stats["tokens_executed"] * 1024  # bit tests the exhaustive passes performed
+    executed = stats["bit_tests_executed"]  # bit tests the exhaustive passes performed
     executed_tbit = executed / (k_ms / max(k_launch, 1) / 1e3) / 1e12
     all_bins_ms = part_ms["all_bins"] / args.steps
     method_bit_tests = rs.n * nb * ntok
@@ -331,7 +349,8 @@ def run_e2e(args, w, st):
     nout = {}
 
     def step():
-        idx = grim.grim_build_host(h["ref"], w["B"], w["q"], w["max_read_len"], stream=st)
+        idx = grim.grim_build_host_ex(h["ref"], w["B"], w["q"], w["max_read_len"],
+                                      coarse_factor=args.coarse_factor, stream=st)
         a = grim.grim_filter_host(idx, h["seq"], h["off"], h["lens"], h["e"], out=outs[0], stream=st)
         b = grim.grim_filter_host(idx, h["seq"], h["off"], h["lens"], h["e"], cand=h["cand"],
                                   cand_off=h["coff"], out=outs[1], stream=st)

@@ -59,8 +59,8 @@ extern "C" {
 /* Bin-major: bin b's 4^q-bit vector is contiguous (Fig. 2 column).  Used by
  * the candidate-list filter. */
 #define GRIM_LAYOUT_BIN_MAJOR 2u
-/* Coarse token-major: the token-major layout over super-bins of
- * GRIM_COARSE_FACTOR adjacent bins.  A super-bin's window is the union of its
+/* Coarse token-major: the token-major layout over super-bins of f adjacent
+ * bins (f = grim_build_opts.coarse_factor; see there for the default).  A super-bin's window is the union of its
  * bins' windows, and because ext >= q-1 every q-gram of that union lies wholly
  * inside one member's window, so a super-bin's vector is exactly the OR of its
  * members' vectors and its token sum bounds each member's from above.  With
@@ -69,7 +69,7 @@ extern "C" {
  * exactly against the bin-major table; the result is identical. */
 #define GRIM_LAYOUT_COARSE 4u
 #define GRIM_LAYOUT_ALL 7u
-#define GRIM_COARSE_FACTOR 2u
+
 
 typedef struct grim_index grim_index; /* opaque; owns its device tables */
 
@@ -118,6 +118,26 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
  * the call. */
 int grim_build_host(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
                     uint32_t layouts, void* stream, grim_index** out);
+
+/* Build options.  Zero-initialise and set what you need. */
+typedef struct {
+  /* bins per super-bin of the coarse table (1..64).  0 chooses the largest
+   * power of two up to 64 whose super-bin window (f*B + ext bases) would
+   * hold at most 40% of all 4^q tokens in a uniform random sequence: 2 at
+   * q = 5, B = 200, ext = 99 and 16 at q = 6, B = 100, ext = 149.  Larger
+   * factors shrink the coarse pass but let more super-bins pass it; the best
+   * value depends on the genome too (the package's autotuner measures it). */
+  uint32_t coarse_factor;
+  uint32_t reserved[7];
+} grim_build_opts;
+
+/* grim_build / grim_build_host with options (opts may be NULL).
+ * Errors: as grim_build, and GRIM_E_ARG for an option out of range. */
+int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
+                  uint32_t layouts, const grim_build_opts* opts, void* stream, grim_index** out);
+int grim_build_host_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q,
+                       uint32_t max_read_len, uint32_t layouts, const grim_build_opts* opts,
+                       void* stream, grim_index** out);
 
 /* Fill *out with the index's sizes and device table pointers. */
 int grim_index_info(const grim_index* idx, grim_index_desc* out);
@@ -233,11 +253,13 @@ typedef struct {
   uint64_t n_reads;          /* reads in the call                                     */
   uint64_t n_records;        /* passing records found (may exceed the call's cap)     */
   uint64_t pairs;            /* (read, bin) pairs decided: reads x bins, or n_cand    */
-  uint64_t tokens_executed;  /* all-bins mode: read tokens applied to 1024-(super-)bin
-                                tiles, counting padding up to a 16-token block; stops
-                                early for a read once every bin of the tile has failed */
+  uint64_t tokens_executed;  /* all-bins mode: read tokens applied to (super-)bin tiles
+                                (1024 wide up to q = 5, 256 at q = 6), counting padding
+                                up to a 16-token block; stops early for a read once
+                                every bin of the tile has failed                       */
   uint64_t survivors;        /* all-bins mode, coarse-then-exact: (read, super-bin)
                                 pairs that passed the coarse pass (0 otherwise)       */
+  uint64_t bit_tests_executed; /* all-bins mode: tokens_executed x (super-)bins per tile */
 } grim_filter_stats;
 
 /* Counters of the calling thread's last successful grim_filter /

@@ -1,6 +1,7 @@
 // C-ABI of libgrim.so (include/grim.h): argument checks, index ownership,
 // workspace layout, the order of kernel launches, status reporting and the
 // optional per-kernel event timing.
+#include <math.h>
 #include <mutex>
 #include <stddef.h>
 #include <string.h>
@@ -11,7 +12,8 @@
 
 struct grim_index {
   grim::IndexView v;   // bins: token-major and bin-major tables
-  grim::IndexView cv;  // super-bins of GRIM_COARSE_FACTOR bins: coarse token-major table
+  grim::IndexView cv;  // super-bins of `factor` bins: coarse token-major table
+  uint32_t factor;
   uint32_t layouts;
   uint32_t* tm;
   uint32_t* bm;
@@ -83,6 +85,21 @@ Layout layout(const IndexView& v, uint32_t n_reads, uint64_t cap, uint32_t coars
   o = align256(o + (coarse_factor ? ((uint64_t)n_reads + 1) * sizeof(uint64_t) : 0));
   L.total = o;
   return L;
+}
+
+// Default bins per super-bin: the largest power of two (2..64) whose
+// super-bin window of f*B + ext bases would hold at most 40% of the 4^q
+// tokens if the sequence were uniform random (1 - exp(-q-grams / 4^q)); a
+// denser coarse table lets too many super-bins pass.  q = 5, B = 200,
+// ext = 99 gives 2; q = 6, B = 100, ext = 149 gives 16.
+uint32_t default_coarse_factor(uint32_t B, uint32_t q, uint32_t ext) {
+  const double tokens = (double)(1u << (2 * q));
+  uint32_t best = 2;
+  for (uint32_t f = 2; f <= 64; f *= 2) {
+    const double grams = (double)f * B + ext - q + 1;
+    if (1.0 - exp(-grams / tokens) <= 0.40) best = f;
+  }
+  return best;
 }
 
 // the all-bins filter can run coarse-then-exact when the index has both the
@@ -196,8 +213,17 @@ const char* grim_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
 int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
                uint32_t layouts, void* stream, grim_index** out) {
+  return grim_build_ex(ref, len, B, q, max_read_len, layouts, nullptr, stream, out);
+}
+
+int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
+                  uint32_t layouts, const grim_build_opts* opts, void* stream, grim_index** out) {
   if (!out) return GRIM_E_ARG;
   *out = nullptr;
+  const uint32_t f = (opts && opts->coarse_factor)
+                         ? opts->coarse_factor
+                         : default_coarse_factor(B, q, max_read_len - 1);
+  if (f > 64) return GRIM_E_ARG;
   if (!ref || len == 0 || B == 0 || max_read_len < q || layouts == 0 ||
       (layouts & ~GRIM_LAYOUT_ALL))
     return GRIM_E_ARG;
@@ -217,16 +243,17 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
   if (v.num_bins > 0xFFFFFFFFull) return GRIM_E_UNSUPPORTED;  // bins are uint32 in the output
   // super-bins: core f*B, the same extension (window = union of f bins' windows)
   IndexView cv = v;
-  cv.B = v.B * GRIM_COARSE_FACTOR;
+  cv.B = v.B * f;
   cv.num_bins = (len + cv.B - 1) / cv.B;
   cv.num_bins_pad = (cv.num_bins + kTileBins - 1) / kTileBins * kTileBins;
   cv.wpad = cv.num_bins_pad / 32;
   // bin-major vectors padded with zero vectors to whole super-bins
-  const uint64_t bm_bins = cv.num_bins * GRIM_COARSE_FACTOR;
+  const uint64_t bm_bins = cv.num_bins * f;
 
   grim_index* ix = new (std::nothrow) grim_index{};
   if (!ix) return GRIM_E_NOMEM;
   ix->layouts = layouts;
+  ix->factor = f;
   auto fail = [&](int code) {
     cudaFree(ix->tm);
     cudaFree(ix->bm);
@@ -298,6 +325,12 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
 
 int grim_build_host(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
                     uint32_t layouts, void* stream, grim_index** out) {
+  return grim_build_host_ex(ref, len, B, q, max_read_len, layouts, nullptr, stream, out);
+}
+
+int grim_build_host_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q,
+                       uint32_t max_read_len, uint32_t layouts, const grim_build_opts* opts,
+                       void* stream, grim_index** out) {
   if (!out) return GRIM_E_ARG;
   *out = nullptr;
   if (!ref || len == 0) return GRIM_E_ARG;
@@ -309,7 +342,7 @@ int grim_build_host(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint3
     cudaFreeAsync(d, st);
     return cuda_fail(e);
   }
-  int rc = grim_build(d, len, B, q, max_read_len, layouts, stream, out);
+  int rc = grim_build_ex(d, len, B, q, max_read_len, layouts, opts, stream, out);
   cudaFreeAsync(d, st);
   e = cudaStreamSynchronize(st);
   if (rc == GRIM_OK && e != cudaSuccess) {
@@ -342,7 +375,7 @@ int grim_index_info(const grim_index* idx, grim_index_desc* out) {
   out->num_coarse_pad = idx->cv.num_bins_pad;
   out->coarse_token_major_bytes =
       idx->ctm ? (uint64_t)idx->cv.r4 * idx->cv.wpad * sizeof(uint32_t) : 0;
-  out->coarse_factor = GRIM_COARSE_FACTOR;
+  out->coarse_factor = idx->factor;
   return GRIM_OK;
 }
 
@@ -359,7 +392,7 @@ uint64_t grim_filter_workspace_size(const grim_index* idx, uint32_t n_reads, uin
                                     uint64_t cap) {
   (void)n_cand;
   if (!idx) return 0;
-  return layout(idx->v, n_reads, cap, two_level_capable(idx) ? GRIM_COARSE_FACTOR : 0).total;
+  return layout(idx->v, n_reads, cap, two_level_capable(idx) ? idx->factor : 0).total;
 }
 
 int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offsets,
@@ -375,13 +408,12 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   const bool capable = two_level_capable(idx);
   if (cand_mode && !(idx->layouts & GRIM_LAYOUT_BIN_MAJOR)) return GRIM_E_NO_LAYOUT;
   if (!cand_mode && !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR) && !capable) return GRIM_E_NO_LAYOUT;
-  if (!cand_mode && idx->v.q > 5) return GRIM_E_UNSUPPORTED;
   if (n_reads == 0) return GRIM_OK;
   if (!reads || !offsets || !lens || !e) return GRIM_E_ARG;
   if (cap && (!out_read || !out_bin || !out_count)) return GRIM_E_ARG;
   if (cap > 0xFFFFFFFFull) return GRIM_E_ARG;
   const IndexView& v = idx->v;
-  const uint32_t f = capable ? GRIM_COARSE_FACTOR : 0;
+  const uint32_t f = capable ? idx->factor : 0;
   const Layout L = layout(v, n_reads, cap, f);
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return GRIM_E_ARG;
   if (workspace_bytes < L.total) return GRIM_E_WORKSPACE;
@@ -426,9 +458,11 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   if (cand_mode) {
     launch_candidates(v, rv, cand, cand_off, ra, ctl, st);
   } else {
-    // all bins: coarse-then-exact when the index allows it and the budget is
-    // small enough for super-bins to fail early; otherwise one exact pass
-    bool two = capable && (h.max_d < 32 || !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR));
+    // all bins: coarse-then-exact when the index allows it and every read
+    // needs enough of its tokens present for super-bins to fail early;
+    // otherwise (some read passes almost anywhere) one exact pass
+    const uint32_t min_slack = 255u - h.max_tight;
+    bool two = capable && (min_slack >= 24 || !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR));
     if (two) {
       const IndexView& cv = idx->cv;
       const uint32_t cbits = cv.num_bins > 1 ? bit_length(cv.num_bins - 1) : 0;
@@ -481,6 +515,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   g_last_stats.n_records = h.n_rec;
   g_last_stats.pairs = cand_mode ? n_cand : (uint64_t)n_reads * v.num_bins;
   g_last_stats.tokens_executed = h.blocks * kBlockTokens;
+  g_last_stats.bit_tests_executed = h.blocks * kBlockTokens * exhaustive_tile_bins(v.r4);
   g_last_stats.survivors = survivors;
   return GRIM_OK;
 }

@@ -4,17 +4,19 @@
 //
 // GB300 mapping
 // -------------
-// * A persistent CTA (512 threads, one per SM) takes work items
-//   (1024-bin tile, range of reads).  The tile -- 4^q rows x 128 B of the
-//   token-major table -- is staged in shared memory once per item and reused
-//   by every read of the range.  Two extra rows follow it: all zeros (for a
-//   q-gram holding a non-base: always a miss) and all ones (padding after a
-//   read's last token: never a miss).
-// * A warp holds four reads, one per quarter warp ("group" of 8 lanes).
-//   Lane i of a group owns words 4i..4i+3 of the tile, i.e. 128 bins, and
-//   fetches them for each token with one 16-byte shared load; a quarter warp
-//   reads one whole 128-byte row, so the four groups' loads of four rows are
-//   four conflict-free wavefronts.
+// * A persistent CTA (one per SM) takes work items (tile of TW*32 bins,
+//   range of reads).  The tile -- 4^q rows x TW words of the token-major
+//   table -- is staged in shared memory once per item and reused by every
+//   read of the range.  TW = 32 (1024 bins, 128 KB at q = 5) up to q = 5 and
+//   TW = 8 (256 bins, 128 KB) at q = 6.  Two extra rows follow the tile: all
+//   zeros (for a q-gram holding a non-base: always a miss) and all ones
+//   (padding after a read's last token: never a miss).
+// * A warp holds 32/GL reads, one per group of GL = TW/4 lanes.  Lane i of a
+//   group owns words 4i..4i+3 of the tile, i.e. 128 bins, and fetches them
+//   for each token with one 16-byte shared load.  At TW = 32 a quarter warp
+//   is one group reading one whole 128-byte row, so the four groups' loads of
+//   four rows are four conflict-free wavefronts; at TW = 8 four groups share
+//   a quarter warp and rows of 32 bytes can collide in a bank group.
 // * Each group copies the token row of the read it will take next into its
 //   own shared-memory slot with cp.async while it works on the current one,
 //   so the inner loop never waits on global memory.
@@ -42,10 +44,9 @@
 namespace grim {
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kGroups = kThreads / 8;
+constexpr int kMaxThreads = 512;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
-constexpr uint32_t kRowBytes = kTileWords * 4;  // one token's row of a tile
+constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 
 #define LOP3(d, a, b, c, lut) \
   asm("lop3.b32 %0, %1, %2, %3, " #lut ";" : "=r"(d) : "r"(a), "r"(b), "r"(c))
@@ -119,7 +120,7 @@ struct ExhArgs {
   uint32_t n_ranges, reads_per_range, n_items;
   uint32_t row_stride;  // bytes of one token row in a group slot (multiple of 16)
   uint32_t slot_bytes;  // bytes of a group slot: two token rows
-  uint32_t c_row, c_hi, c_lo;  // 128, 65536, -65536: multipliers of the address math
+  uint32_t c_row, c_hi, c_lo;  // TW*4, 65536, -65536: multipliers of the address math
   Ctl* ctl;
 };
 
@@ -172,23 +173,28 @@ __device__ __forceinline__ void add_block(Counters<P>& c, const uint32_t (&tw)[8
   }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
-  // [tile: (r4 + 2) rows x 128 B][64 group slots][16 padding tokens]
+template <int P, int TW>
+__global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
+  constexpr uint32_t kRowBytes = TW * 4;     // one token's row of a tile
+  constexpr uint32_t GL = TW / 4;            // lanes per group (one read)
+  constexpr uint32_t kGroupMask = (1u << GL) - 1u;
+  constexpr uint32_t kTileBinsT = TW * 32;
+  // [tile: (r4 + 2) rows x TW words][group slots][16 padding tokens]
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint32_t s_item, s_next;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, grp = lane >> 3, li = lane & 7;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, grp = lane / GL, li = lane % GL;
+  const uint32_t nthreads = blockDim.x;
   const uint32_t r4 = a.ix.r4;
   if (*(volatile uint32_t*)&a.ctl->status) return;  // set by the tokeniser before launch
 
   uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem);
   const uint32_t tile_bytes = (r4 + 2) * kRowBytes;
   const uint32_t sh_base = (uint32_t)__cvta_generic_to_shared(smem);
-  const uint32_t slot = sh_base + tile_bytes + (tid >> 3) * a.slot_bytes;
-  const uint32_t pad_tokens = sh_base + tile_bytes + kGroups * a.slot_bytes;
-  for (uint32_t i = tid; i < kTileWords; i += kThreads) {
-    s_tile[rowInvalid(r4) * kTileWords + i] = 0u;
-    s_tile[rowPad(r4) * kTileWords + i] = ~0u;
+  const uint32_t slot = sh_base + tile_bytes + (tid / GL) * a.slot_bytes;
+  const uint32_t pad_tokens = sh_base + tile_bytes + (nthreads / GL) * a.slot_bytes;
+  for (uint32_t i = tid; i < (uint32_t)TW; i += nthreads) {
+    s_tile[rowInvalid(r4) * TW + i] = 0u;
+    s_tile[rowPad(r4) * TW + i] = ~0u;
   }
   if (tid < 2) {  // 16 padding tokens = 32 bytes
     const uint32_t pp = rowPad(r4) | (rowPad(r4) << 16);
@@ -211,11 +217,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
     const uint32_t r0 = range * a.reads_per_range;
     const uint32_t nr = min(a.reads_per_range, a.rv.n_reads - r0);
 
-    // stage the tile: rows [0, r4), words [tile*32, tile*32+32)
+    // stage the tile: rows [0, r4), words [tile*TW, tile*TW+TW)
     {
-      const uint32_t* src = a.ix.tm + (uint64_t)tile * kTileWords;
-      for (uint32_t i = tid; i < r4 * 8u; i += kThreads) {
-        const uint32_t row = i >> 3, chunk = i & 7u;
+      constexpr uint32_t kChunks = TW / 4;  // 16-byte chunks per row
+      const uint32_t* src = a.ix.tm + (uint64_t)tile * TW;
+      for (uint32_t i = tid; i < r4 * kChunks; i += nthreads) {
+        const uint32_t row = i / kChunks, chunk = i % kChunks;
         const uint32_t* g = src + (uint64_t)row * a.ix.wpad + chunk * 4u;
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sh_base + row * kRowBytes +
                                                                       chunk * 16u),
@@ -228,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
     uint32_t vmask[4];
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-      const uint64_t b0 = (uint64_t)tile * kTileBins + (li * 4u + w) * 32u;
+      const uint64_t b0 = (uint64_t)tile * kTileBinsT + (li * 4u + w) * 32u;
       const uint64_t left = b0 < a.ix.num_bins ? a.ix.num_bins - b0 : 0;
       vmask[w] = left >= 32 ? ~0u : ((1u << left) - 1u);
     }
@@ -245,12 +252,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
     {
       uint32_t k = 0;
       if (li == 0) k = atomicAdd(&s_next, 1u);
-      k = __shfl_sync(0xFFFFFFFFu, k, grp * 8);
+      k = __shfl_sync(0xFFFFFFFFu, k, grp * GL);
       if (k < nr) {
         nxt = r0 + k;
         nxt_meta = __ldg(a.rv.meta + nxt);
         const char* src = reinterpret_cast<const char*>(a.rv.tokens + (uint64_t)nxt * a.rv.ts);
-        for (uint32_t ch = li; ch < row_chunks; ch += 8)
+        for (uint32_t ch = li; ch < row_chunks; ch += GL)
           asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(slot + ch * 16u),
                        "l"(src + ch * 16u));
       }
@@ -283,14 +290,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
         const bool take = need && !fin;
         uint32_t k = 0;
         if (take && li == 0) k = atomicAdd(&s_next, 1u);
-        k = __shfl_sync(0xFFFFFFFFu, k, grp * 8);
+        k = __shfl_sync(0xFFFFFFFFu, k, grp * GL);
         if (take) {
           nxt = k < nr ? r0 + k : kNone;
           if (nxt != kNone) {
             nxt_meta = __ldg(a.rv.meta + nxt);
             const char* src = reinterpret_cast<const char*>(a.rv.tokens + (uint64_t)nxt * a.rv.ts);
             const uint32_t dst = slot + (buf ^ 1u) * a.row_stride;
-            for (uint32_t ch = li; ch < row_chunks; ch += 8)
+            for (uint32_t ch = li; ch < row_chunks; ch += GL)
               asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst + ch * 16u),
                            "l"(src + ch * 16u));
           }
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
       // (3) a read ends when every bin of its tile is dead or its tokens are used up
       const uint32_t all_dead = c.dead[0] & c.dead[1] & c.dead[2] & c.dead[3];
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, all_dead == ~0u);
-      const bool gdead = ((bal >> (grp * 8)) & 0xFFu) == 0xFFu;
+      const bool gdead = ((bal >> (grp * GL)) & kGroupMask) == kGroupMask;
       const bool done = !fin && (gdead || blk >= nblk);
       const bool emit = done && !gdead;
       if (__any_sync(0xFFFFFFFFu, emit)) {
@@ -343,7 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
             const uint32_t bit = __ffs(m) - 1;
             m &= m - 1;
             const uint32_t misses = c.value(w, bit) - bias;
-            const uint64_t bin = (uint64_t)tile * kTileBins + (li * 4u + w) * 32u + bit;
+            const uint64_t bin = (uint64_t)tile * kTileBinsT + (li * 4u + w) * 32u + bit;
             if (pos < a.rec.cap) {
               a.rec.keys[pos] = ((unsigned long long)cur << a.bin_bits) | bin;
               a.rec.counts[pos] = (uint8_t)(ntok - misses);
@@ -354,61 +361,77 @@ __global__ void __launch_bounds__(kThreads, 1) k_exhaustive(ExhArgs a) {
       }
       if (done) cur = kNone;
     }
-    // one count per group (its 8 lanes agree), one atomic per warp and item
+    // one count per group (its lanes agree), one atomic per warp and item
     uint32_t ex = li == 0 ? executed : 0u;
     ex = __reduce_add_sync(0xFFFFFFFFu, ex);
     if (lane == 0 && ex) atomicAdd(&a.ctl->blocks, (unsigned long long)ex);
   }
 }
 
-template <int P>
-void launch_p(const ExhArgs& a, size_t smem, uint32_t grid, cudaStream_t st, const char* name) {
-  cudaFuncSetAttribute(k_exhaustive<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int P, int TW>
+void launch_p(const ExhArgs& a, size_t smem, uint32_t threads, uint32_t grid, cudaStream_t st,
+              const char* name) {
+  cudaFuncSetAttribute(k_exhaustive<P, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   ProfScope ps(name, st);
-  k_exhaustive<P><<<grid, kThreads, smem, st>>>(a);
+  k_exhaustive<P, TW><<<grid, threads, smem, st>>>(a);
+}
+
+template <int TW>
+void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, cudaStream_t st,
+               const char* name) {
+  constexpr uint32_t kRowBytes = TW * 4, GL = TW / 4, kTileBinsT = TW * 32;
+  const uint32_t n_tiles = (uint32_t)(ix.num_bins_pad / kTileBinsT);
+  // enough items to balance the persistent grid, each range at least 64 reads
+  uint32_t n_ranges = (uint32_t)((4u * sms + n_tiles - 1) / n_tiles);
+  const uint32_t max_ranges = (a.rv.n_reads + 63) / 64;
+  if (n_ranges > max_ranges) n_ranges = max_ranges;
+  if (n_ranges < 1) n_ranges = 1;
+  const uint32_t per = (a.rv.n_reads + n_ranges - 1) / n_ranges;
+  n_ranges = (a.rv.n_reads + per - 1) / per;
+  a.n_ranges = n_ranges;
+  a.reads_per_range = per;
+  a.n_items = n_tiles * n_ranges;
+  a.c_row = kRowBytes;
+  // the largest CTA whose tile and group slots fit in shared memory
+  const size_t tile_bytes = (size_t)(ix.r4 + 2) * kRowBytes;
+  uint32_t threads = kMaxThreads;
+  while (threads > 64 && tile_bytes + (size_t)(threads / GL) * a.slot_bytes + 32 > kSmemLimit)
+    threads /= 2;
+  const size_t smem = tile_bytes + (size_t)(threads / GL) * a.slot_bytes + 32;
+  uint32_t grid = sms;
+  if (grid > a.n_items) grid = a.n_items;
+  // the counters need 2^P > D' (D' <= 255)
+  if (max_d < 32) launch_p<5, TW>(a, smem, threads, grid, st, name);
+  else if (max_d < 64) launch_p<6, TW>(a, smem, threads, grid, st, name);
+  else if (max_d < 128) launch_p<7, TW>(a, smem, threads, grid, st, name);
+  else launch_p<8, TW>(a, smem, threads, grid, st, name);
 }
 
 }  // namespace
 
+uint32_t exhaustive_tile_bins(uint32_t r4) { return r4 <= 1024 ? 32u * 32u : 8u * 32u; }
+
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st, const char* prof_name) {
   if (rv.n_reads == 0) return;
-  const uint32_t n_tiles = (uint32_t)(ix.num_bins_pad / kTileBins);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms <= 0) sms = 1;
-  // enough items to balance the persistent grid, each range at least 64 reads
-  uint32_t n_ranges = (uint32_t)((4u * (uint32_t)sms + n_tiles - 1) / n_tiles);
-  const uint32_t max_ranges = (rv.n_reads + 63) / 64;
-  if (n_ranges > max_ranges) n_ranges = max_ranges;
-  if (n_ranges < 1) n_ranges = 1;
-  const uint32_t per = (rv.n_reads + n_ranges - 1) / n_ranges;
-  n_ranges = (rv.n_reads + per - 1) / per;
   ExhArgs a{};
   a.ix = ix;
   a.rv = rv;
   a.rec = rec;
   a.bin_bits = bin_bits;
-  a.n_ranges = n_ranges;
-  a.reads_per_range = per;
-  a.n_items = n_tiles * n_ranges;
   a.row_stride = rv.ts * 2u;
-  // slots of consecutive groups start 32 bytes apart modulo 128, so the four
+  // slots of consecutive groups start 32 bytes apart modulo 128, so the
   // groups of a warp mostly read their tokens from different banks
   a.slot_bytes = (2u * a.row_stride + 127u) / 128u * 128u + 32u;
-  a.c_row = kRowBytes;
   a.c_hi = 65536u;
   a.c_lo = 0u - 65536u;
   a.ctl = ctl;
-  const size_t smem = (size_t)(ix.r4 + 2) * kRowBytes + (size_t)kGroups * a.slot_bytes + 32;
-  uint32_t grid = (uint32_t)sms;
-  if (grid > a.n_items) grid = a.n_items;
-  // the counters need 2^P > D' (D' <= 255)
-  if (max_d < 32) launch_p<5>(a, smem, grid, st, prof_name);
-  else if (max_d < 64) launch_p<6>(a, smem, grid, st, prof_name);
-  else if (max_d < 128) launch_p<7>(a, smem, grid, st, prof_name);
-  else launch_p<8>(a, smem, grid, st, prof_name);
+  if (ix.r4 <= 1024) launch_tw<32>(a, ix, max_d, (uint32_t)sms, st, prof_name);
+  else launch_tw<8>(a, ix, max_d, (uint32_t)sms, st, prof_name);
 }
 
 }  // namespace grim

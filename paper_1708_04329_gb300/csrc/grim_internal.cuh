@@ -25,7 +25,8 @@ struct Ctl {
   uint32_t item;              // work-item counter of the persistent filter kernels
   unsigned long long blocks;  // 16-token blocks applied to 1024-bin tiles (all-bins mode)
   uint32_t max_d;             // largest miss budget D' = min(q*e, L-q+1) of the batch
-  uint32_t pad[57];
+  uint32_t max_tight;         // 255 - the smallest slack (L-q+1) - D' of the batch
+  uint32_t pad[56];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte slot");
 
@@ -85,6 +86,8 @@ void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t*
 void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
                              uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st);
 
+// bins per tile of the all-bins kernel for a table of r4 = 4^q rows
+uint32_t exhaustive_tile_bins(uint32_t r4);
 // max_d: the batch's largest miss budget (sizes the bit-sliced counters)
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st,

@@ -66,8 +66,11 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
     uint32_t d = q * (uint32_t)e[r];
     if (d > ntok) d = ntok;
     meta[r] = ntok | (d << 8);
-    // most batches share one budget: skip the atomic once the max is reached
+    // most batches share one budget: skip the atomics once the max is reached
     if (d > *reinterpret_cast<volatile uint32_t*>(&ctl->max_d)) atomicMax(&ctl->max_d, d);
+    const uint32_t tight = 255u - (ntok - d);
+    if (tight > *reinterpret_cast<volatile uint32_t*>(&ctl->max_tight))
+      atomicMax(&ctl->max_tight, tight);
   }
 }
 

@@ -33,14 +33,13 @@ GRIM_LAYOUT_BIN_MAJOR = 2
 GRIM_LAYOUT_BOTH = 3
 GRIM_LAYOUT_COARSE = 4
 GRIM_LAYOUT_ALL = 7
-GRIM_COARSE_FACTOR = 2
 
 #: every symbol include/grim.h declares
 EXPORTS = (
     "grim_build", "grim_build_host", "grim_index_info", "grim_free", "grim_strerror",
     "grim_last_cuda_error", "grim_filter_workspace_size", "grim_filter", "grim_filter_host",
     "grim_loc_to_bin", "grim_edits_for_rate", "grim_profile", "grim_profile_get",
-    "grim_filter_noalloc", "grim_last_filter_stats",
+    "grim_filter_noalloc", "grim_last_filter_stats", "grim_build_ex", "grim_build_host_ex",
 )
 
 
@@ -66,7 +65,12 @@ class _Desc(C.Structure):
 
 class _Stats(C.Structure):
     _fields_ = [("n_reads", C.c_uint64), ("n_records", C.c_uint64), ("pairs", C.c_uint64),
-                ("tokens_executed", C.c_uint64), ("survivors", C.c_uint64)]
+                ("tokens_executed", C.c_uint64), ("survivors", C.c_uint64),
+                ("bit_tests_executed", C.c_uint64)]
+
+
+class _BuildOpts(C.Structure):
+    _fields_ = [("coarse_factor", C.c_uint32), ("reserved", C.c_uint32 * 7)]
 
 
 class _KTime(C.Structure):
@@ -88,6 +92,11 @@ def _lib() -> C.CDLL:
         lib.grim_build.argtypes = [vp, u64, u32, u32, u32, u32, vp, pp]
         lib.grim_build_host.restype = i32
         lib.grim_build_host.argtypes = [vp, u64, u32, u32, u32, u32, vp, pp]
+        lib.grim_build_ex.restype = i32
+        lib.grim_build_ex.argtypes = [vp, u64, u32, u32, u32, u32, C.POINTER(_BuildOpts), vp, pp]
+        lib.grim_build_host_ex.restype = i32
+        lib.grim_build_host_ex.argtypes = [vp, u64, u32, u32, u32, u32, C.POINTER(_BuildOpts), vp,
+                                           pp]
         lib.grim_index_info.restype = i32
         lib.grim_index_info.argtypes = [vp, C.POINTER(_Desc)]
         lib.grim_free.restype = None
@@ -283,6 +292,33 @@ def grim_build_host(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_
     rc = _lib().grim_build_host(p, n, B, q, max_read_len, layouts, _stream_ptr(stream), C.byref(h))
     if rc != GRIM_OK:
         raise GrimError(rc, "grim_build_host")
+    return GrimIndex(h.value)
+
+
+def grim_build_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
+                  coarse_factor: int = 0, stream=None) -> GrimIndex:
+    """grim_build_ex: grim_build with build options (``coarse_factor``: bins per
+    super-bin of the coarse table, 0 = the library default)."""
+    opts = _BuildOpts(coarse_factor)
+    h = C.c_void_p()
+    rc = _lib().grim_build_ex(_dptr(ref, "ref", 1), ref.numel(), B, q, max_read_len, layouts,
+                              C.byref(opts), _stream_ptr(stream), C.byref(h))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_build_ex")
+    return GrimIndex(h.value)
+
+
+def grim_build_host_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
+                       coarse_factor: int = 0, stream=None) -> GrimIndex:
+    """grim_build_host_ex: grim_build_host with build options."""
+    p, keep = _hptr(ref, "ref", np.uint8)
+    n = keep.numel() if hasattr(keep, "numel") else keep.size
+    opts = _BuildOpts(coarse_factor)
+    h = C.c_void_p()
+    rc = _lib().grim_build_host_ex(p, n, B, q, max_read_len, layouts, C.byref(opts),
+                                   _stream_ptr(stream), C.byref(h))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_build_host_ex")
     return GrimIndex(h.value)
 
 

@@ -14,12 +14,15 @@ def dev_reads(rs):
                 e=torch.from_numpy(np.ascontiguousarray(rs.e, np.uint16).view(np.int16)).cuda())
 
 
-def build(genome: np.ndarray, B: int, q: int, mrl: int, layouts: int = 7):
+def build(genome: np.ndarray, B: int, q: int, mrl: int, layouts: int = 7, coarse_factor: int = 0):
     import torch
 
     from paper_1708_04329_gb300 import grim
 
-    return grim.grim_build(torch.from_numpy(np.ascontiguousarray(genome)).cuda(), B, q, mrl, layouts)
+    ref = torch.from_numpy(np.ascontiguousarray(genome)).cuda()
+    if coarse_factor:
+        return grim.grim_build_ex(ref, B, q, mrl, layouts, coarse_factor)
+    return grim.grim_build(ref, B, q, mrl, layouts)
 
 
 def gpu_filter(idx, rs, cand_off=None, cand=None, cap=None, workspace=None):

@@ -10,11 +10,9 @@ import pytest
 import oracle
 from tests.conftest import Reads, random_case
 
-F = 2  # GRIM_COARSE_FACTOR
-
-
+@pytest.mark.parametrize("F", [2, 3, 5])
 @pytest.mark.parametrize("seed", range(6))
-def test_super_bin_vector_is_or_of_members(seed):
+def test_super_bin_vector_is_or_of_members(seed, F):
     rng = np.random.default_rng(40 + seed)
     q = int(rng.choice([2, 3, 4, 5]))
     B = int(rng.integers(3, 50))
@@ -30,8 +28,9 @@ def test_super_bin_vector_is_or_of_members(seed):
         assert np.array_equal(coarse.vecs[s], np.bitwise_or.reduce(members, axis=0)), s
 
 
+@pytest.mark.parametrize("F", [2, 4])
 @pytest.mark.parametrize("seed", range(4))
-def test_super_bin_sum_bounds_member_sums(seed):
+def test_super_bin_sum_bounds_member_sums(seed, F):
     rng = np.random.default_rng(60 + seed)
     q = int(rng.choice([3, 4, 5]))
     B = int(rng.integers(5, 40))

@@ -33,8 +33,8 @@ def _gpu_tables(idx, q):
             None if bm is None else bm.cpu().numpy().view(np.uint32))
 
 
-def _check_tables(ref: np.ndarray, B: int, q: int, mrl: int, layouts: int = 7):
-    idx = build(ref, B, q, mrl, layouts)
+def _check_tables(ref: np.ndarray, B: int, q: int, mrl: int, layouts: int = 7, factor: int = 0):
+    idx = build(ref, B, q, mrl, layouts, factor)
     tm, bm = _gpu_tables(idx, q)
     oix = oracle.bin_vectors(ref, B, q, mrl)
     vb = oracle.vector_bytes(q)
@@ -46,8 +46,9 @@ def _check_tables(ref: np.ndarray, B: int, q: int, mrl: int, layouts: int = 7):
         assert np.array_equal(tm, oracle.token_major(oix))
     ctm = idx.coarse_token_major()
     if ctm is not None:
-        # super-bins of 2 bins: the oracle's vectors with core 2B, same extension
-        coarse = oracle.bin_vectors(ref, 2 * B, q, mrl)
+        # super-bins of f bins: the oracle's vectors with core f*B, same extension
+        f = idx.desc.coarse_factor
+        coarse = oracle.bin_vectors(ref, f * B, q, mrl)
         assert np.array_equal(ctm.cpu().numpy().view(np.uint32), oracle.token_major(coarse))
         assert idx.desc.num_coarse == coarse.num_bins
     d = idx.desc
@@ -115,7 +116,7 @@ def test_random_all_bins(seed, layouts):
     per-read e including T <= 0; one exact pass over the token-major table
     (layouts 1), coarse-then-exact (6), or whichever the batch suits (7)."""
     rng = np.random.default_rng(500 + seed)
-    q = int(rng.choice([2, 3, 4, 5]))
+    q = int(rng.choice([2, 3, 4, 5, 6]))
     B = int(rng.integers(5, 40))
     mrl = int(rng.integers(max(q, 20), 120))
     n = int(rng.integers(30_000, 90_000))
@@ -291,10 +292,34 @@ def test_filter_host_equals_oracle():
     assert_same(got, oracle.filter(oix, rs, cand_off=off, cand=cand))
 
 
-def test_q6_all_bins_reports_unsupported():
-    from paper_1708_04329_gb300 import grim
+@pytest.mark.parametrize("layouts", [1, 6, 7])
+def test_q6_all_bins(layouts):
+    """q = 6 (4096-row table, 256-bin tiles): several tiles plus a ragged one."""
+    from paper_1708_04329_gb300 import synth
 
-    idx = build(_np("ACGTACGTACGT" * 20), 10, 6, 12)
-    with pytest.raises(grim.GrimError) as ei:
-        gpu_filter(idx, Reads(["ACGTACGT"], [0]))
-    assert ei.value.code == grim.GRIM_E_UNSUPPORTED
+    g = synth.human_genome(400_000, seed=8)
+    rs = synth.reads(g, 700, seed=9, lengths=(150,), e=7, max_edits=7)
+    idx, oix = _check_tables(g, 100, 6, 150, layouts)
+    if layouts & 4:  # default factor: the largest power of two keeping a window near 40% full
+        assert idx.desc.coarse_factor == 16
+    assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
+
+
+def test_default_coarse_factor_q5():
+    from paper_1708_04329_gb300 import synth
+
+    g = synth.genome(50_000, seed=2)
+    assert build(g, 200, 5, 100).desc.coarse_factor == 2
+
+
+@pytest.mark.parametrize("q,factor", [(4, 3), (5, 4), (5, 7), (6, 8), (6, 16)])
+def test_coarse_factors(q, factor):
+    """Coarse-then-exact with super-bins of 3..16 bins (ragged last super-bin)."""
+    rng = np.random.default_rng(900 + factor)
+    B = int(rng.integers(20, 60))
+    mrl = 120
+    ref, reads, e = random_case(rng, q, 90_001, B, mrl, 300)
+    rs = Reads(reads, e)
+    idx, oix = _check_tables(_np(ref), B, q, mrl, layouts=6, factor=factor)
+    assert idx.desc.coarse_factor == factor
+    assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
