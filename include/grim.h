@@ -49,6 +49,7 @@ extern "C" {
 #define GRIM_E_WORKSPACE (-9)      /* workspace smaller than grim_filter_workspace_size()       */
 #define GRIM_E_NO_LAYOUT (-10)     /* the index lacks the table layout this call needs          */
 #define GRIM_E_UNSUPPORTED (-11)   /* parameter outside what this build implements              */
+#define GRIM_E_NOT_READY (-12)     /* grim_plan_query: the plan's last launch is still running  */
 
 /* ---- table layouts (bit mask for grim_build) ----------------------------- */
 /* Token-major: row t holds token t's bit for every bin, contiguous
@@ -238,6 +239,69 @@ int grim_filter_noalloc(const grim_index* idx, const char* reads, const uint64_t
                         const int32_t* cand, const uint64_t* cand_off, uint64_t n_cand,
                         uint32_t* out_read, uint32_t* out_bin, uint8_t* out_count, uint64_t cap,
                         uint64_t* n_out, void* stream);
+
+/* ---- graph-captured plans for ragged batches ---------------------------- */
+/*
+ * A plan runs grim_filter's work for batches of up to declared maximum sizes
+ * as one CUDA graph: every launch shape is fixed at creation, the batch's
+ * counts are copied to the device at the start of each run, and the choices
+ * grim_filter makes on the host between launches (coarse-then-exact or one
+ * exact pass, survivor overflow, sort sizes) are made by the kernels from
+ * device-resident counts.  Reads of any lengths up to the index's
+ * max_read_len and, in candidate mode, ragged candidate lists are handled in
+ * that single graph launch per batch.  Results are identical to grim_filter.
+ *
+ * The plan owns device buffers for one batch's inputs and outputs
+ * (grim_plan_buffers_get); the caller fills them (for example with
+ * cudaMemcpyAsync on the launch stream) before grim_plan_launch.  One launch
+ * of a plan may be in flight at a time: grim_plan_launch waits for the
+ * previous one to finish; use several plans to overlap batches.
+ */
+typedef struct grim_plan grim_plan;
+
+#define GRIM_PLAN_CANDIDATES 1u /* candidate-list mode (else all bins) */
+
+typedef struct {
+  uint32_t max_reads;   /* reads per batch, >= 1                                    */
+  uint32_t max_e;       /* largest per-read edit budget (sizes the counters); a read
+                           with a larger e makes that batch fail with GRIM_E_ARG    */
+  uint64_t max_bases;   /* bytes of read sequence per batch, >= 1                   */
+  uint64_t max_cand;    /* candidate mode: candidates per batch                     */
+  uint64_t cap;         /* output records per batch                                 */
+  uint32_t flags;       /* GRIM_PLAN_*                                              */
+  uint32_t reserved[7];
+} grim_plan_desc;
+
+/* Device buffers owned by a plan (layouts as for grim_filter). */
+typedef struct {
+  char* reads;          /* [max_bases]                                 */
+  uint64_t* offsets;    /* [max_reads]                                 */
+  uint32_t* lens;       /* [max_reads]                                 */
+  uint16_t* e;          /* [max_reads]                                 */
+  int32_t* cand;        /* [max_cand], candidate mode only, else NULL  */
+  uint64_t* cand_off;   /* [max_reads + 1], candidate mode only        */
+  uint32_t* out_read;   /* [cap]                                       */
+  uint32_t* out_bin;    /* [cap]                                       */
+  uint8_t* out_count;   /* [cap]                                       */
+} grim_plan_buffers;
+
+/* Allocate a plan's buffers (cudaMalloc, pinned host memory) and capture its
+ * graph.  The index must outlive the plan.
+ * Errors: GRIM_E_ARG, GRIM_E_NO_LAYOUT, GRIM_E_NOMEM, GRIM_E_CUDA. */
+int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_plan** out);
+int grim_plan_buffers_get(const grim_plan* plan, grim_plan_buffers* out);
+/* Enqueue one run on `stream` for a batch of n_reads reads (and n_cand
+ * candidates) already in the plan's buffers.  Asynchronous. */
+int grim_plan_launch(grim_plan* plan, uint32_t n_reads, uint64_t n_cand, void* stream);
+/* GRIM_OK if the last launch has finished (or none was made),
+ * GRIM_E_NOT_READY if it is still running. */
+int grim_plan_query(const grim_plan* plan);
+/* Wait for the last launch; *n_out = passing records in the output buffers.
+ * Errors of the batch as for grim_filter (GRIM_E_OVERFLOW: *n_out = total). */
+int grim_plan_wait(grim_plan* plan, uint64_t* n_out);
+/* Device bytes the plan holds (inputs, outputs and workspace). */
+uint64_t grim_plan_device_bytes(const grim_plan* plan);
+void grim_plan_free(grim_plan* plan);
 
 /* ---- helpers of the mapper around the filter (§GRIM-Filter, Fig. 5) ----- */
 

@@ -29,6 +29,7 @@ GRIM_SOURCES = [
     "grim_candidates.cu",
     "grim_compact.cu",
     "grim_noalloc.cu",
+    "grim_plan.cu",
 ]
 GRIM_HEADERS = ["grim_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -10,17 +10,6 @@
 
 #include "grim_internal.cuh"
 
-struct grim_index {
-  grim::IndexView v;   // bins: token-major and bin-major tables
-  grim::IndexView cv;  // super-bins of `factor` bins: coarse token-major table
-  uint32_t factor;
-  uint32_t layouts;
-  uint32_t* tm;
-  uint32_t* bm;
-  uint32_t* ctm;
-  uint32_t* presence;
-};
-
 namespace grim {
 namespace {
 
@@ -38,55 +27,6 @@ int cuda_fail(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
-inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
-
-// token stride: the longest read's token count rounded up to a 16-token block
-inline uint32_t token_stride(const IndexView& v) {
-  const uint32_t nt = v.max_read_len - v.q + 1;
-  return (nt + kBlockTokens - 1) / kBlockTokens * kBlockTokens;
-}
-
-struct Layout {
-  uint64_t tok, meta, keys_a, keys_b, cnt_a, cnt_b, hist, cand, cand_off, total;
-};
-
-// Survivors of the coarse pass get their own capacity: reads from repeat
-// families survive in many super-bins that then fail the exact check.
-constexpr uint64_t kSurvivorsPerRead = 64;
-
-inline uint64_t record_capacity(uint32_t n_reads, uint64_t cap, uint32_t coarse_factor) {
-  const uint64_t s = coarse_factor ? kSurvivorsPerRead * n_reads : 0;
-  return s > cap ? s : cap;
-}
-
-// coarse_factor > 0: room for the coarse pass's survivors and for the
-// candidate lists they expand into (coarse_factor per survivor)
-Layout layout(const IndexView& v, uint32_t n_reads, uint64_t cap, uint32_t coarse_factor) {
-  Layout L{};
-  const uint64_t rcap = record_capacity(n_reads, cap, coarse_factor);
-  uint64_t o = sizeof(Ctl);
-  L.tok = o;
-  o = align256(o + (uint64_t)n_reads * token_stride(v) * sizeof(uint16_t));
-  L.meta = o;
-  o = align256(o + (uint64_t)n_reads * sizeof(uint32_t));
-  L.keys_a = o;
-  o = align256(o + rcap * sizeof(unsigned long long));
-  L.keys_b = o;
-  o = align256(o + rcap * sizeof(unsigned long long));
-  L.cnt_a = o;
-  o = align256(o + rcap);
-  L.cnt_b = o;
-  o = align256(o + rcap);
-  L.hist = o;
-  o = align256(o + sort_workspace_bytes(rcap));
-  L.cand = o;
-  o = align256(o + (coarse_factor ? rcap * coarse_factor * sizeof(int32_t) : 0));
-  L.cand_off = o;
-  o = align256(o + (coarse_factor ? ((uint64_t)n_reads + 1) * sizeof(uint64_t) : 0));
-  L.total = o;
-  return L;
-}
-
 // Default bins per super-bin: the largest power of two (2..64) whose
 // super-bin window of f*B + ext bases would hold at most 40% of the 4^q
 // tokens if the sequence were uniform random (1 - exp(-q-grams / 4^q)); a
@@ -100,21 +40,6 @@ uint32_t default_coarse_factor(uint32_t B, uint32_t q, uint32_t ext) {
     if (1.0 - exp(-grams / tokens) <= 0.40) best = f;
   }
   return best;
-}
-
-// the all-bins filter can run coarse-then-exact when the index has both the
-// coarse table and the bin-major table
-bool two_level_capable(const grim_index* idx) {
-  return (idx->layouts & GRIM_LAYOUT_COARSE) && (idx->layouts & GRIM_LAYOUT_BIN_MAJOR);
-}
-
-int status_to_code(uint32_t s) {
-  if (s & kStatusShort) return GRIM_E_READ_TOO_SHORT;
-  if (s & kStatusLong) return GRIM_E_READ_TOO_LONG;
-  if (s & kStatusBadCsr) return GRIM_E_ARG;
-  if (s & kStatusBadCand) return GRIM_E_BAD_CANDIDATE;
-  if (s & kStatusTimeout) return GRIM_E_TIMEOUT;
-  return GRIM_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -131,6 +56,7 @@ struct Pending {
 };
 std::mutex g_prof_mu;
 bool g_prof_on = false;
+thread_local bool g_prof_suspended = false;
 std::vector<ProfEntry> g_prof;
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_event_pool;
@@ -148,7 +74,10 @@ cudaEvent_t take_event() {
 
 }  // namespace
 
+void prof_suspend(bool on) { g_prof_suspended = on; }
+
 ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), st(s) {
+  if (g_prof_suspended) return;
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return;
   int idx = -1;
@@ -205,6 +134,7 @@ const char* grim_strerror(int s) {
     case GRIM_E_WORKSPACE: return "workspace too small";
     case GRIM_E_NO_LAYOUT: return "index lacks the table layout this call needs";
     case GRIM_E_UNSUPPORTED: return "parameter outside what this build implements";
+    case GRIM_E_NOT_READY: return "the plan's last launch is still running";
     default: return "unknown status";
   }
 }

@@ -49,6 +49,7 @@ struct CandArgs {
   const uint64_t* cand_off;
   RecordsView rec;
   Ctl* ctl;
+  Live live;
 };
 
 constexpr int kWarps = 8;
@@ -65,12 +66,14 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
   const uint32_t sub = lane % G;     // this lane's slice of a bin vector
   const uint32_t slot = lane / G;    // which of the warp's CPW candidates
   if (*(volatile uint32_t*)&a.ctl->status) return;
+  if (gated_off(a.ctl, a.live)) return;  // the batch takes the other path
+  const uint32_t n_reads = live_reads(a.ctl, a.live, a.rv.n_reads);
 
   for (;;) {
     uint32_t r = 0;
     if (lane == 0) r = atomicAdd(&a.ctl->item, 1u);
     r = __shfl_sync(0xFFFFFFFFu, r, 0);
-    if (r >= a.rv.n_reads) break;
+    if (r >= n_reads) break;
     const uint64_t c0 = a.cand_off[r], c1 = a.cand_off[r + 1];
     if (c0 == c1) continue;
 
@@ -179,9 +182,9 @@ void launch_t(const CandArgs& a, cudaStream_t st, const char* name) {
 
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
                        const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
-                       const char* prof_name) {
+                       const char* prof_name, Live live) {
   if (rv.n_reads == 0) return;
-  CandArgs a{ix, rv, cand, cand_off, rec, ctl};
+  CandArgs a{ix, rv, cand, cand_off, rec, ctl, live};
   switch (ix.wpb) {
     case 1: launch_t<1>(a, st, prof_name); break;
     case 2: launch_t<2>(a, st, prof_name); break;

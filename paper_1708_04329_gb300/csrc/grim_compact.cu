@@ -19,10 +19,26 @@ constexpr uint32_t kSortThreads = 256;
 constexpr uint32_t kSortItems = 16;  // per thread per pass
 constexpr uint32_t kSortTile = kSortThreads * kSortItems;
 
+// Live record counts: *n_live (capped at n) when n_live is set, else n; a
+// gate (ctl, path) makes the kernel a no-op unless the batch took that path.
+__device__ __forceinline__ uint64_t live_n(const unsigned long long* n_live, uint64_t n) {
+  if (!n_live) return n;
+  const uint64_t v = *reinterpret_cast<const volatile unsigned long long*>(n_live);
+  return v < n ? v : n;
+}
+__device__ __forceinline__ bool gate_off(const Ctl* c, uint32_t gate) {
+  return c && gate && *reinterpret_cast<const volatile uint32_t*>(&c->path) != gate;
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const unsigned long long* __restrict__ keys,
                                                           uint64_t n, uint32_t shift,
-                                                          uint32_t* __restrict__ hist, uint32_t nb) {
+                                                          uint32_t* __restrict__ hist, uint32_t nb,
+                                                          const unsigned long long* n_live,
+                                                          const Ctl* gc, uint32_t gate) {
   __shared__ uint32_t cnt[256];
+  if (gate_off(gc, gate)) return;
+  n = live_n(n_live, n);
+  if ((uint64_t)blockIdx.x * kSortTile >= n) return;  // past the live records
   cnt[threadIdx.x] = 0;
   __syncthreads();
   const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
@@ -34,15 +50,28 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const unsigned long lo
   hist[(uint64_t)threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Exclusive scan of m counters with one block: thread t owns a contiguous
-// segment, scans its sums across the block, then rewrites its segment.
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ h, uint64_t m) {
+// Exclusive scan, with one block, of the digit-major histogram of the live
+// blocks: entry (d, blk) at h[d * nb + blk] for blk < nb_live.  Thread t owns
+// a contiguous segment of the 256 * nb_live entries, scans its sums across
+// the block, then rewrites its segment.
+__device__ __forceinline__ uint64_t hist_at(uint64_t i, uint64_t nb_live, uint64_t nb) {
+  return (i / nb_live) * nb + (i % nb_live);
+}
+
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ h, uint64_t nb, uint64_t n,
+                                                  const unsigned long long* n_live, const Ctl* gc,
+                                                  uint32_t gate) {
   __shared__ uint32_t part[1024];
+  if (gate_off(gc, gate)) return;
+  n = live_n(n_live, n);
+  const uint64_t nb_live = (n + kSortTile - 1) / kSortTile;
+  if (nb_live == 0) return;
+  const uint64_t m = 256 * nb_live;
   const uint64_t per = (m + 1023) / 1024;
   const uint64_t lo = threadIdx.x * per;
   const uint64_t hi = lo + per < m ? lo + per : m;
   uint32_t s = 0;
-  for (uint64_t i = lo; i < hi; ++i) s += h[i];
+  for (uint64_t i = lo; i < hi; ++i) s += h[hist_at(i, nb_live, nb)];
   part[threadIdx.x] = s;
   __syncthreads();
   for (uint32_t d = 1; d < 1024; d <<= 1) {
@@ -53,8 +82,9 @@ __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ h, uint
   }
   uint32_t run = part[threadIdx.x] - s;
   for (uint64_t i = lo; i < hi; ++i) {
-    const uint32_t v = h[i];
-    h[i] = run;
+    const uint64_t j = hist_at(i, nb_live, nb);
+    const uint32_t v = h[j];
+    h[j] = run;
     run += v;
   }
 }
@@ -62,10 +92,14 @@ __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ h, uint
 __global__ void __launch_bounds__(kSortThreads) k_rs_scatter(
     const unsigned long long* __restrict__ kin, const uint8_t* __restrict__ cin,
     unsigned long long* __restrict__ kout, uint8_t* __restrict__ cout, uint64_t n, uint32_t shift,
-    const uint32_t* __restrict__ hist, uint32_t nb) {
+    const uint32_t* __restrict__ hist, uint32_t nb, const unsigned long long* n_live, const Ctl* gc,
+    uint32_t gate) {
   constexpr uint32_t kW = kSortThreads / 32;
   __shared__ uint32_t s_base[256];
   __shared__ uint32_t s_wcnt[kW][256];
+  if (gate_off(gc, gate)) return;
+  n = live_n(n_live, n);
+  if ((uint64_t)blockIdx.x * kSortTile >= n) return;  // past the live records
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   s_base[tid] = hist[(uint64_t)tid * nb + blockIdx.x];
   const uint64_t base = (uint64_t)blockIdx.x * kSortTile;
@@ -101,9 +135,12 @@ __global__ void k_emit(const unsigned long long* __restrict__ keys,
                        uint32_t bin_bits, const int32_t* __restrict__ cand,
                        const uint64_t* __restrict__ cand_off, uint32_t n_reads,
                        uint32_t* __restrict__ out_read, uint32_t* __restrict__ out_bin,
-                       uint8_t* __restrict__ out_count) {
+                       uint8_t* __restrict__ out_count, const unsigned long long* n_live,
+                       const uint32_t* n_reads_live, const Ctl* gc, uint32_t gate) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (gate_off(gc, gate)) return;
+  if (i >= live_n(n_live, n)) return;
+  if (n_reads_live) n_reads = *reinterpret_cast<const volatile uint32_t*>(n_reads_live);
   const unsigned long long key = keys[i];
   uint32_t r, b;
   if (cand_mode) {
@@ -131,8 +168,13 @@ __global__ void k_emit(const unsigned long long* __restrict__ keys,
 // the number of survivors of reads before r.
 __global__ void k_expand(const unsigned long long* __restrict__ keys, uint64_t n_surv,
                          uint32_t cbits, uint32_t f, uint32_t n_reads, int32_t* __restrict__ cand,
-                         uint64_t* __restrict__ cand_off) {
+                         uint64_t* __restrict__ cand_off, const Ctl* lc, uint32_t gate) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (lc) {
+    if (gate_off(lc, gate)) return;
+    n_surv = *reinterpret_cast<const volatile unsigned long long*>(&lc->n_surv);
+    n_reads = *reinterpret_cast<const volatile uint32_t*>(&lc->live_reads);
+  }
   const unsigned long long mask = cbits >= 64 ? ~0ull : ((1ull << cbits) - 1ull);
   if (i < n_surv) {
     const uint32_t s = (uint32_t)(keys[i] & mask);
@@ -158,15 +200,17 @@ uint64_t sort_workspace_bytes(uint64_t cap) {
 }
 
 void expand_survivors(const unsigned long long* keys, uint64_t n_surv, uint32_t cbits, uint32_t f,
-                      uint32_t n_reads, int32_t* cand, uint64_t* cand_off, cudaStream_t st) {
+                      uint32_t n_reads, int32_t* cand, uint64_t* cand_off, cudaStream_t st,
+                      const Ctl* live_ctl, uint32_t gate) {
   const uint64_t n = n_surv > (uint64_t)n_reads + 1 ? n_surv : (uint64_t)n_reads + 1;
   ProfScope ps("expand", st);
   k_expand<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, n_surv, cbits, f, n_reads, cand,
-                                                       cand_off);
+                                                       cand_off, live_ctl, gate);
 }
 
 RecordsView sort_records(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
-                         cudaStream_t st) {
+                         cudaStream_t st, const unsigned long long* n_live, const Ctl* gate_ctl,
+                         uint32_t gate) {
   if (n == 0) return a;
   const uint32_t nb = (uint32_t)((n + kSortTile - 1) / kSortTile);
   uint32_t* h = static_cast<uint32_t*>(hist);
@@ -176,16 +220,16 @@ RecordsView sort_records(RecordsView a, RecordsView b, uint64_t n, uint32_t key_
     const uint32_t shift = 8 * p;
     {
       ProfScope ps("sort_hist", st);
-      k_rs_hist<<<nb, kSortThreads, 0, st>>>(src.keys, n, shift, h, nb);
+      k_rs_hist<<<nb, kSortThreads, 0, st>>>(src.keys, n, shift, h, nb, n_live, gate_ctl, gate);
     }
     {
       ProfScope ps("sort_scan", st);
-      k_rs_scan<<<1, 1024, 0, st>>>(h, 256ull * nb);
+      k_rs_scan<<<1, 1024, 0, st>>>(h, nb, n, n_live, gate_ctl, gate);
     }
     {
       ProfScope ps("sort_scatter", st);
       k_rs_scatter<<<nb, kSortThreads, 0, st>>>(src.keys, src.counts, dst.keys, dst.counts, n,
-                                                shift, h, nb);
+                                                shift, h, nb, n_live, gate_ctl, gate);
     }
     RecordsView t = src;
     src = dst;
@@ -197,13 +241,16 @@ RecordsView sort_records(RecordsView a, RecordsView b, uint64_t n, uint32_t key_
 void sort_and_emit(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
                    bool candidate_mode, uint32_t bin_bits, const int32_t* cand,
                    const uint64_t* cand_off, uint32_t n_reads, uint32_t* out_read,
-                   uint32_t* out_bin, uint8_t* out_count, cudaStream_t st) {
+                   uint32_t* out_bin, uint8_t* out_count, cudaStream_t st,
+                   const unsigned long long* n_live, const uint32_t* n_reads_live,
+                   const Ctl* gate_ctl, uint32_t gate) {
   if (n == 0) return;
-  const RecordsView src = sort_records(a, b, n, key_bits, hist, st);
+  const RecordsView src = sort_records(a, b, n, key_bits, hist, st, n_live, gate_ctl, gate);
   ProfScope ps("emit", st);
   k_emit<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src.keys, src.counts, n, candidate_mode,
                                                       bin_bits, cand, cand_off, n_reads, out_read,
-                                                      out_bin, out_count);
+                                                      out_bin, out_count, n_live, n_reads_live,
+                                                      gate_ctl, gate);
 }
 
 }  // namespace grim

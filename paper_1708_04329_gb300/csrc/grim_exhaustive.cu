@@ -117,7 +117,8 @@ struct ExhArgs {
   ReadsView rv;
   RecordsView rec;
   uint32_t bin_bits;
-  uint32_t n_ranges, reads_per_range, n_items;
+  uint32_t n_tiles, sms;
+  Live live;
   uint32_t row_stride;  // bytes of one token row in a group slot (multiple of 16)
   uint32_t slot_bytes;  // bytes of a group slot: two token rows
   uint32_t c_row, c_hi, c_lo;  // TW*4, 65536, -65536: multipliers of the address math
@@ -186,6 +187,17 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
   const uint32_t nthreads = blockDim.x;
   const uint32_t r4 = a.ix.r4;
   if (*(volatile uint32_t*)&a.ctl->status) return;  // set by the tokeniser before launch
+  if (gated_off(a.ctl, a.live)) return;             // the batch takes the other path
+  // work items: (tile, range of reads); enough of them to balance the
+  // persistent grid, each range at least 64 reads
+  const uint32_t n_reads = live_reads(a.ctl, a.live, a.rv.n_reads);
+  if (n_reads == 0) return;
+  uint32_t n_ranges = (4u * a.sms + a.n_tiles - 1) / a.n_tiles;
+  n_ranges = min(n_ranges, (n_reads + 63) / 64);
+  n_ranges = max(n_ranges, 1u);
+  const uint32_t per = (n_reads + n_ranges - 1) / n_ranges;
+  n_ranges = (n_reads + per - 1) / per;
+  const uint32_t n_items = a.n_tiles * n_ranges;
 
   uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem);
   const uint32_t tile_bytes = (r4 + 2) * kRowBytes;
@@ -212,10 +224,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
     }
     __syncthreads();
     const uint32_t item = s_item;
-    if (item >= a.n_items) break;
-    const uint32_t tile = item / a.n_ranges, range = item % a.n_ranges;
-    const uint32_t r0 = range * a.reads_per_range;
-    const uint32_t nr = min(a.reads_per_range, a.rv.n_reads - r0);
+    if (item >= n_items) break;
+    const uint32_t tile = item / n_ranges, range = item % n_ranges;
+    const uint32_t r0 = range * per;
+    const uint32_t nr = min(per, n_reads - r0);
 
     // stage the tile: rows [0, r4), words [tile*TW, tile*TW+TW)
     {
@@ -380,17 +392,8 @@ template <int TW>
 void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, cudaStream_t st,
                const char* name) {
   constexpr uint32_t kRowBytes = TW * 4, GL = TW / 4, kTileBinsT = TW * 32;
-  const uint32_t n_tiles = (uint32_t)(ix.num_bins_pad / kTileBinsT);
-  // enough items to balance the persistent grid, each range at least 64 reads
-  uint32_t n_ranges = (uint32_t)((4u * sms + n_tiles - 1) / n_tiles);
-  const uint32_t max_ranges = (a.rv.n_reads + 63) / 64;
-  if (n_ranges > max_ranges) n_ranges = max_ranges;
-  if (n_ranges < 1) n_ranges = 1;
-  const uint32_t per = (a.rv.n_reads + n_ranges - 1) / n_ranges;
-  n_ranges = (a.rv.n_reads + per - 1) / per;
-  a.n_ranges = n_ranges;
-  a.reads_per_range = per;
-  a.n_items = n_tiles * n_ranges;
+  a.n_tiles = (uint32_t)(ix.num_bins_pad / kTileBinsT);
+  a.sms = sms;
   a.c_row = kRowBytes;
   // the largest CTA whose tile and group slots fit in shared memory
   const size_t tile_bytes = (size_t)(ix.r4 + 2) * kRowBytes;
@@ -398,8 +401,14 @@ void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, cu
   while (threads > 64 && tile_bytes + (size_t)(threads / GL) * a.slot_bytes + 32 > kSmemLimit)
     threads /= 2;
   const size_t smem = tile_bytes + (size_t)(threads / GL) * a.slot_bytes + 32;
+  // small batches on few tiles need fewer CTAs (graph launches size for the
+  // largest batch and let surplus CTAs find no work)
   uint32_t grid = sms;
-  if (grid > a.n_items) grid = a.n_items;
+  if (!a.live.on) {
+    const uint32_t per_item = 64;
+    const uint64_t items = (uint64_t)a.n_tiles * ((a.rv.n_reads + per_item - 1) / per_item);
+    if (items < grid) grid = (uint32_t)(items ? items : 1);
+  }
   // the counters need 2^P > D' (D' <= 255)
   if (max_d < 32) launch_p<5, TW>(a, smem, threads, grid, st, name);
   else if (max_d < 64) launch_p<6, TW>(a, smem, threads, grid, st, name);
@@ -412,7 +421,8 @@ void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, cu
 uint32_t exhaustive_tile_bins(uint32_t r4) { return r4 <= 1024 ? 32u * 32u : 8u * 32u; }
 
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
-                       uint32_t max_d, Ctl* ctl, cudaStream_t st, const char* prof_name) {
+                       uint32_t max_d, Ctl* ctl, cudaStream_t st, const char* prof_name,
+                       Live live) {
   if (rv.n_reads == 0) return;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -423,6 +433,7 @@ void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec
   a.rv = rv;
   a.rec = rec;
   a.bin_bits = bin_bits;
+  a.live = live;
   a.row_stride = rv.ts * 2u;
   // slots of consecutive groups start 32 bytes apart modulo 128, so the
   // groups of a warp mostly read their tokens from different banks

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "grim.h"
@@ -23,18 +24,44 @@ struct Ctl {
   unsigned long long n_rec;   // passing records found (may exceed cap)
   uint32_t status;            // kStatus* bits
   uint32_t item;              // work-item counter of the persistent filter kernels
-  unsigned long long blocks;  // 16-token blocks applied to 1024-bin tiles (all-bins mode)
+  unsigned long long blocks;  // 16-token blocks applied to (super-)bin tiles (all-bins mode)
   uint32_t max_d;             // largest miss budget D' = min(q*e, L-q+1) of the batch
   uint32_t max_tight;         // 255 - the smallest slack (L-q+1) - D' of the batch
-  uint32_t pad[56];
+  // graph launches (grim_plan): the batch's counts and the path taken live
+  // on the device, so no launch depends on a host read-back
+  uint32_t live_reads;             // reads in this batch
+  uint32_t path;                   // kPathCoarse / kPathExact
+  unsigned long long live_cand;    // candidates in this batch
+  unsigned long long n_surv;       // survivors of the coarse pass
+  unsigned long long n_final;      // passing records of the batch
+  uint32_t pad[48];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte slot");
+static_assert(offsetof(Ctl, live_reads) == 32, "live counts follow the per-pass counters");
+constexpr uint32_t kPathCoarse = 1u;  // coarse pass, then exact check of the survivors
+constexpr uint32_t kPathExact = 2u;   // one exact pass over every bin
+
+// Counts a kernel works on: fixed by the host (grim_filter), or read from
+// the control block at run time (graph launches).  `gate`, when nonzero, is
+// the path the kernel belongs to: it returns at once unless ctl->path == gate.
+struct Live {
+  bool on;
+  uint32_t gate;
+};
+__device__ __forceinline__ uint32_t live_reads(const Ctl* c, const Live& l, uint32_t host_n) {
+  return l.on ? *reinterpret_cast<const volatile uint32_t*>(&c->live_reads) : host_n;
+}
+__device__ __forceinline__ bool gated_off(const Ctl* c, const Live& l) {
+  return l.on && l.gate && *reinterpret_cast<const volatile uint32_t*>(&c->path) != l.gate;
+}
 
 constexpr uint32_t kStatusShort = 1u;     // read with L < q
 constexpr uint32_t kStatusLong = 2u;      // read with L > max_read_len or > 255 tokens
 constexpr uint32_t kStatusBadCand = 4u;   // candidate outside [0, num_bins)
 constexpr uint32_t kStatusBadCsr = 8u;    // CSR offsets decreasing or not ending at n_cand
 constexpr uint32_t kStatusTimeout = 16u;  // bounded wait gave up
+constexpr uint32_t kStatusArg = 32u;      // a read's e exceeds the plan's declared maximum
+constexpr uint32_t kStatusSurv = 64u;     // coarse survivors exceed their capacity (no exact table)
 
 // Token buffer entries are table row indices: a token value t < 4^q, or
 // rowInvalid(q) for a q-gram with a non-base (adds a miss: the zero row), or
@@ -80,33 +107,43 @@ void launch_build_token_major(const uint32_t* codes, const uint32_t* invalid, co
 void launch_row_popcount(const uint32_t* tm, uint32_t rows, uint64_t words_per_row,
                          uint32_t* presence, cudaStream_t st);
 
+// max_e: reads with a larger budget are an argument error (graph launches
+// fix the counter depth from it); 0xFFFF = no limit
 void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t* lens,
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
-                     uint32_t* meta, Ctl* ctl, cudaStream_t st);
+                     uint32_t* meta, Ctl* ctl, cudaStream_t st, Live live = {false, 0},
+                     uint32_t max_e = 0xFFFFu);
 void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
-                             uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st);
+                             uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st,
+                             Live live = {false, 0});
 
 // bins per tile of the all-bins kernel for a table of r4 = 4^q rows
 uint32_t exhaustive_tile_bins(uint32_t r4);
 // max_d: the batch's largest miss budget (sizes the bit-sliced counters)
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st,
-                       const char* prof_name = "exhaustive");
+                       const char* prof_name = "exhaustive", Live live = {false, 0});
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
                        const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
-                       const char* prof_name = "candidates");
+                       const char* prof_name = "candidates", Live live = {false, 0});
 
 // Radix sort of n (key, count) records by the low key_bits bits of the key,
 // followed by the split into the caller's (read, bin, count) arrays.
 uint64_t sort_workspace_bytes(uint64_t cap);
+// n_live (nullable): the record count is read on the device from *n_live,
+// capped at n; n then only sizes the launches
 RecordsView sort_records(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
-                         cudaStream_t st);  // returns whichever of a, b holds the sorted keys
+                         cudaStream_t st, const unsigned long long* n_live = nullptr,
+                         const Ctl* gate_ctl = nullptr, uint32_t gate = 0);
 void expand_survivors(const unsigned long long* keys, uint64_t n_surv, uint32_t cbits, uint32_t f,
-                      uint32_t n_reads, int32_t* cand, uint64_t* cand_off, cudaStream_t st);
+                      uint32_t n_reads, int32_t* cand, uint64_t* cand_off, cudaStream_t st,
+                      const Ctl* live_ctl = nullptr, uint32_t gate = 0);
 void sort_and_emit(RecordsView a, RecordsView b, uint64_t n, uint32_t key_bits, void* hist,
                    bool candidate_mode, uint32_t bin_bits, const int32_t* cand,
                    const uint64_t* cand_off, uint32_t n_reads, uint32_t* out_read,
-                   uint32_t* out_bin, uint8_t* out_count, cudaStream_t st);
+                   uint32_t* out_bin, uint8_t* out_count, cudaStream_t st,
+                   const unsigned long long* n_live = nullptr, const uint32_t* n_reads_live = nullptr,
+                   const Ctl* gate_ctl = nullptr, uint32_t gate = 0);
 
 // ---------------------------------------------------------------------------
 // per-kernel timing (grim_profile): wraps one launch in events on `st`
@@ -118,6 +155,7 @@ struct ProfScope {
   cudaStream_t st;
 };
 void prof_collect();  // resolve finished events into the totals (after a sync)
+void prof_suspend(bool on);  // no event timing while a graph is being captured
 
 inline uint32_t bit_length(uint64_t v) {
   uint32_t b = 0;
@@ -125,4 +163,84 @@ inline uint32_t bit_length(uint64_t v) {
   return b;
 }
 
+// ---------------------------------------------------------------------------
+// the index and the filter workspace (shared by grim_api.cu and grim_plan.cu)
+// ---------------------------------------------------------------------------
+inline uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
+
+// token stride: the longest read's token count rounded up to a 16-token block
+inline uint32_t token_stride(const IndexView& v) {
+  const uint32_t nt = v.max_read_len - v.q + 1;
+  return (nt + kBlockTokens - 1) / kBlockTokens * kBlockTokens;
+}
+
+struct Layout {
+  uint64_t tok, meta, keys_a, keys_b, cnt_a, cnt_b, hist, cand, cand_off, total;
+};
+
+// Survivors of the coarse pass get their own capacity: reads from repeat
+// families survive in many super-bins that then fail the exact check.
+constexpr uint64_t kSurvivorsPerRead = 64;
+
+inline uint64_t record_capacity(uint32_t n_reads, uint64_t cap, uint32_t coarse_factor) {
+  const uint64_t s = coarse_factor ? kSurvivorsPerRead * n_reads : 0;
+  return s > cap ? s : cap;
+}
+
+// coarse_factor > 0: room for the coarse pass's survivors and for the
+// candidate lists they expand into (coarse_factor per survivor)
+inline Layout layout(const IndexView& v, uint32_t n_reads, uint64_t cap, uint32_t coarse_factor) {
+  Layout L{};
+  const uint64_t rcap = record_capacity(n_reads, cap, coarse_factor);
+  uint64_t o = sizeof(Ctl);
+  L.tok = o;
+  o = align256(o + (uint64_t)n_reads * token_stride(v) * sizeof(uint16_t));
+  L.meta = o;
+  o = align256(o + (uint64_t)n_reads * sizeof(uint32_t));
+  L.keys_a = o;
+  o = align256(o + rcap * sizeof(unsigned long long));
+  L.keys_b = o;
+  o = align256(o + rcap * sizeof(unsigned long long));
+  L.cnt_a = o;
+  o = align256(o + rcap);
+  L.cnt_b = o;
+  o = align256(o + rcap);
+  L.hist = o;
+  o = align256(o + sort_workspace_bytes(rcap));
+  L.cand = o;
+  o = align256(o + (coarse_factor ? rcap * coarse_factor * sizeof(int32_t) : 0));
+  L.cand_off = o;
+  o = align256(o + (coarse_factor ? ((uint64_t)n_reads + 1) * sizeof(uint64_t) : 0));
+  L.total = o;
+  return L;
+}
+
+inline int status_to_code(uint32_t s) {
+  if (s & kStatusShort) return GRIM_E_READ_TOO_SHORT;
+  if (s & kStatusLong) return GRIM_E_READ_TOO_LONG;
+  if ((s & kStatusBadCsr) || (s & kStatusArg)) return GRIM_E_ARG;
+  if (s & kStatusBadCand) return GRIM_E_BAD_CANDIDATE;
+  if (s & kStatusTimeout) return GRIM_E_TIMEOUT;
+  return GRIM_OK;
+}
+
+}  // namespace grim
+
+struct grim_index {
+  grim::IndexView v;   // bins: token-major and bin-major tables
+  grim::IndexView cv;  // super-bins of `factor` bins: coarse token-major table
+  uint32_t factor;
+  uint32_t layouts;
+  uint32_t* tm;
+  uint32_t* bm;
+  uint32_t* ctm;
+  uint32_t* presence;
+};
+
+namespace grim {
+// the all-bins filter can run coarse-then-exact when the index has both the
+// coarse table and the bin-major table
+inline bool two_level_capable(const grim_index* idx) {
+  return (idx->layouts & GRIM_LAYOUT_COARSE) && (idx->layouts & GRIM_LAYOUT_BIN_MAJOR);
+}
 }  // namespace grim

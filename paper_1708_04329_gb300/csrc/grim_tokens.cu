@@ -23,12 +23,14 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
     const char* __restrict__ reads, const uint64_t* __restrict__ offsets,
     const uint32_t* __restrict__ lens, const uint16_t* __restrict__ e, uint32_t n_reads, uint32_t q,
     uint32_t max_read_len, uint32_t r4, uint32_t ts, const uint32_t* __restrict__ presence,
-    uint16_t* __restrict__ tokens, uint32_t* __restrict__ meta, Ctl* ctl) {
+    uint16_t* __restrict__ tokens, uint32_t* __restrict__ meta, Ctl* ctl, Live live,
+    uint32_t max_e) {
   __shared__ unsigned long long s_key[kTokWarps][kMaxStride];
   __shared__ uint16_t s_row[kTokWarps][kMaxStride];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-  if (r >= n_reads) return;  // whole warps only: the warp syncs below stay uniform
+  if (r >= live_reads(ctl, live, n_reads)) return;  // whole warps: warp syncs stay uniform
+  if (e[r] > max_e && lane == 0) atomicOr(&ctl->status, kStatusArg);
   const uint32_t L = lens[r];
   const uint64_t off = offsets[r];
   uint16_t* out = tokens + r * ts;
@@ -76,8 +78,12 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
 
 __global__ void k_check_candidates(const int32_t* __restrict__ cand,
                                    const uint64_t* __restrict__ cand_off, uint32_t n_reads,
-                                   uint64_t n_cand, uint64_t num_bins, Ctl* ctl) {
+                                   uint64_t n_cand, uint64_t num_bins, Ctl* ctl, Live live) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (live.on) {
+    n_reads = *reinterpret_cast<volatile uint32_t*>(&ctl->live_reads);
+    n_cand = *reinterpret_cast<volatile unsigned long long*>(&ctl->live_cand);
+  }
   if (i < n_cand) {
     int32_t b = cand[i];
     if (b < 0 || (uint64_t)b >= num_bins) atomicOr(&ctl->status, kStatusBadCand);
@@ -92,23 +98,24 @@ __global__ void k_check_candidates(const int32_t* __restrict__ cand,
 
 void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t* lens,
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
-                     uint32_t* meta, Ctl* ctl, cudaStream_t st) {
+                     uint32_t* meta, Ctl* ctl, cudaStream_t st, Live live, uint32_t max_e) {
   if (rv.n_reads == 0) return;
   const uint32_t threads = kTokWarps * 32;
   uint64_t grid = ((uint64_t)rv.n_reads * 32 + threads - 1) / threads;
   ProfScope ps("tokenise", st);
   k_tokenise<<<(unsigned)grid, threads, 0, st>>>(reads, offsets, lens, e, rv.n_reads, ix.q,
                                                  ix.max_read_len, ix.r4, rv.ts, ix.presence, tokens,
-                                                 meta, ctl);
+                                                 meta, ctl, live, max_e);
 }
 
 void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
-                             uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st) {
+                             uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st,
+                             Live live) {
   uint64_t n = n_cand > n_reads ? n_cand : n_reads;
   if (n == 0) n = 1;
   ProfScope ps("check_candidates", st);
   k_check_candidates<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, cand_off, n_reads, n_cand,
-                                                                  num_bins, ctl);
+                                                                  num_bins, ctl, live);
 }
 
 }  // namespace grim

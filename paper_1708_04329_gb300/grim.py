@@ -27,6 +27,8 @@ GRIM_E_TIMEOUT = -8
 GRIM_E_WORKSPACE = -9
 GRIM_E_NO_LAYOUT = -10
 GRIM_E_UNSUPPORTED = -11
+GRIM_E_NOT_READY = -12
+GRIM_PLAN_CANDIDATES = 1
 
 GRIM_LAYOUT_TOKEN_MAJOR = 1
 GRIM_LAYOUT_BIN_MAJOR = 2
@@ -40,6 +42,8 @@ EXPORTS = (
     "grim_last_cuda_error", "grim_filter_workspace_size", "grim_filter", "grim_filter_host",
     "grim_loc_to_bin", "grim_edits_for_rate", "grim_profile", "grim_profile_get",
     "grim_filter_noalloc", "grim_last_filter_stats", "grim_build_ex", "grim_build_host_ex",
+    "grim_plan_create", "grim_plan_buffers_get", "grim_plan_launch", "grim_plan_query",
+    "grim_plan_wait", "grim_plan_device_bytes", "grim_plan_free",
 )
 
 
@@ -71,6 +75,17 @@ class _Stats(C.Structure):
 
 class _BuildOpts(C.Structure):
     _fields_ = [("coarse_factor", C.c_uint32), ("reserved", C.c_uint32 * 7)]
+
+
+class _PlanDesc(C.Structure):
+    _fields_ = [("max_reads", C.c_uint32), ("max_e", C.c_uint32), ("max_bases", C.c_uint64),
+                ("max_cand", C.c_uint64), ("cap", C.c_uint64), ("flags", C.c_uint32),
+                ("reserved", C.c_uint32 * 7)]
+
+
+class _PlanBuffers(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("reads", "offsets", "lens", "e", "cand", "cand_off",
+                                           "out_read", "out_bin", "out_count")]
 
 
 class _KTime(C.Structure):
@@ -120,6 +135,20 @@ def _lib() -> C.CDLL:
         lib.grim_edits_for_rate.argtypes = [u32, u32, u32]
         lib.grim_last_filter_stats.restype = i32
         lib.grim_last_filter_stats.argtypes = [C.POINTER(_Stats)]
+        lib.grim_plan_create.restype = i32
+        lib.grim_plan_create.argtypes = [vp, C.POINTER(_PlanDesc), pp]
+        lib.grim_plan_buffers_get.restype = i32
+        lib.grim_plan_buffers_get.argtypes = [vp, C.POINTER(_PlanBuffers)]
+        lib.grim_plan_launch.restype = i32
+        lib.grim_plan_launch.argtypes = [vp, u32, u64, vp]
+        lib.grim_plan_query.restype = i32
+        lib.grim_plan_query.argtypes = [vp]
+        lib.grim_plan_wait.restype = i32
+        lib.grim_plan_wait.argtypes = [vp, C.POINTER(C.c_uint64)]
+        lib.grim_plan_device_bytes.restype = u64
+        lib.grim_plan_device_bytes.argtypes = [vp]
+        lib.grim_plan_free.restype = None
+        lib.grim_plan_free.argtypes = [vp]
         lib.grim_profile.restype = i32
         lib.grim_profile.argtypes = [i32]
         lib.grim_profile_get.restype = i32
@@ -513,3 +542,134 @@ def grim_filter_noalloc(index: GrimIndex, reads, offsets, lens, e, out, cand=Non
         raise err
     n = int(n_out.value)
     return out[0][:n], out[1][:n], out[2][:n]
+
+
+# ---------------------------------------------------------------------------
+# graph-captured plans
+# ---------------------------------------------------------------------------
+
+class GrimPlan:
+    """Owns a grim_plan handle (and keeps its index alive)."""
+
+    def __init__(self, handle: int, index: GrimIndex, desc: _PlanDesc):
+        self._h = handle
+        self.index = index
+        self.max_reads = int(desc.max_reads)
+        self.max_bases = int(desc.max_bases)
+        self.max_cand = int(desc.max_cand)
+        self.cap = int(desc.cap)
+        self.candidates = bool(desc.flags & GRIM_PLAN_CANDIDATES)
+        self.buffers = grim_plan_buffers_get(self)
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("plan already freed")
+        return self._h
+
+    def close(self) -> None:
+        if self._h:
+            _lib().grim_plan_free(self._h)
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stage(self, reads, offsets, lens, e, cand=None, cand_off=None):
+        """Copy one batch (CUDA or pinned CPU tensors) into the plan's buffers
+        on the current stream."""
+        b = self.buffers
+        n = int(lens.numel())
+        nb = int(reads.numel())
+        if n > self.max_reads or nb > self.max_bases:
+            raise ValueError("batch larger than the plan")
+        b["reads"][:nb].copy_(reads.view(b["reads"].dtype), non_blocking=True)
+        b["offsets"][:n].copy_(offsets.view(b["offsets"].dtype), non_blocking=True)
+        b["lens"][:n].copy_(lens.view(b["lens"].dtype), non_blocking=True)
+        b["e"][:n].copy_(e.view(b["e"].dtype), non_blocking=True)
+        if self.candidates:
+            nc = int(cand.numel())
+            if nc > self.max_cand:
+                raise ValueError("more candidates than the plan holds")
+            b["cand"][:nc].copy_(cand.view(b["cand"].dtype), non_blocking=True)
+            b["cand_off"][:n + 1].copy_(cand_off.view(b["cand_off"].dtype), non_blocking=True)
+            return n, nc
+        return n, 0
+
+    def run(self, reads, offsets, lens, e, cand=None, cand_off=None, stream=None):
+        """stage + launch + wait; returns (read, bin, count) views of the
+        plan's output buffers (valid until the plan's next launch)."""
+        n, nc = self.stage(reads, offsets, lens, e, cand, cand_off)
+        grim_plan_launch(self, n, nc, stream)
+        k = grim_plan_wait(self)
+        b = self.buffers
+        return b["out_read"][:k], b["out_bin"][:k], b["out_count"][:k]
+
+
+def grim_plan_create(index: GrimIndex, max_reads: int, max_bases: int, max_e: int, cap: int,
+                     max_cand: int = 0, candidates: bool = False) -> GrimPlan:
+    d = _PlanDesc(max_reads, max_e, max_bases, max_cand, cap,
+                  GRIM_PLAN_CANDIDATES if candidates else 0)
+    h = C.c_void_p()
+    rc = _lib().grim_plan_create(index.handle, C.byref(d), C.byref(h))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_plan_create")
+    return GrimPlan(h.value, index, d)
+
+
+def grim_plan_buffers_get(plan: GrimPlan) -> dict:
+    """The plan's device buffers as zero-copy CUDA tensors."""
+    torch = _torch()
+    b = _PlanBuffers()
+    rc = _lib().grim_plan_buffers_get(plan.handle, C.byref(b))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_plan_buffers_get")
+    spec = {"reads": (plan.max_bases, "|u1"), "offsets": (plan.max_reads, "<i8"),
+            "lens": (plan.max_reads, "<i4"), "e": (plan.max_reads, "<i2"),
+            "cand": (plan.max_cand, "<i4"), "cand_off": (plan.max_reads + 1, "<i8"),
+            "out_read": (plan.cap, "<i4"), "out_bin": (plan.cap, "<i4"),
+            "out_count": (plan.cap, "|u1")}
+    out = {}
+    for name, (n, ts) in spec.items():
+        ptr = getattr(b, name)
+        if ptr and n:
+            out[name] = torch.as_tensor(_CudaArray(ptr, (n,), ts, plan), device="cuda")
+    return out
+
+
+def grim_plan_launch(plan: GrimPlan, n_reads: int, n_cand: int = 0, stream=None) -> None:
+    rc = _lib().grim_plan_launch(plan.handle, n_reads, n_cand, _stream_ptr(stream))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_plan_launch")
+
+
+def grim_plan_query(plan: GrimPlan) -> bool:
+    """True when the plan's last launch has finished."""
+    rc = _lib().grim_plan_query(plan.handle)
+    if rc == GRIM_E_NOT_READY:
+        return False
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_plan_query")
+    return True
+
+
+def grim_plan_wait(plan: GrimPlan) -> int:
+    """Wait for the last launch; returns the number of passing records."""
+    n_out = C.c_uint64(0)
+    rc = _lib().grim_plan_wait(plan.handle, C.byref(n_out))
+    if rc != GRIM_OK:
+        err = GrimError(rc, "grim_plan_wait")
+        err.n_out = int(n_out.value)
+        raise err
+    return int(n_out.value)
+
+
+def grim_plan_device_bytes(plan: GrimPlan) -> int:
+    return int(_lib().grim_plan_device_bytes(plan.handle))
+
+
+def grim_plan_free(plan: GrimPlan) -> None:
+    plan.close()
