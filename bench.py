@@ -52,9 +52,10 @@ def parse_args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--workload", default="human", choices=["human", "finer"],
+    p.add_argument("--workload", default="human", choices=["human", "finer", "ragged"],
                    help="human: B=200, q=5, L=100, e=5 (the headline); finer: B=100, q=6, "
-                        "L=150, e=7 on the same genome")
+                        "L=150, e=7 on the same genome; ragged: candidate lists for reads of "
+                        "mixed length and budget through one graph-captured plan")
     p.add_argument("--coarse-factor", type=int, default=0,
                    help="bins per super-bin of the coarse table (0: the library's choice)")
     p.add_argument("--genome", type=int, default=3_100_000_000, help="reference length (bases)")
@@ -435,11 +436,139 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_ragged(args, rank, world, local):
+    """Ragged candidate lists: L in {100,150,250}, per-read e, LogNormal lists.
+    One step = one launch of a graph-captured plan over the whole batch
+    (inputs staged in the plan's buffers before timing); the plain grim_filter
+    call on the same device inputs is timed beside it."""
+    import torch
+
+    from paper_1708_04329_gb300 import autotune, grim, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n_reads = args.reads if args.reads != 1_000_000 else 4_000_000
+    t0 = time.perf_counter()
+    g = synth.human_genome(args.genome)
+    w = synth.ragged_candidates(n_reads=n_reads, g=g)
+    if rank:
+        w["reads"] = synth.reads(g, n_reads, seed=4 + 7919 * rank, lengths=(100, 150, 250),
+                                 probs=(0.5, 0.3, 0.2), e_frac=(5, 100), max_edits=None)
+        nb0 = (len(g) + w["B"] - 1) // w["B"]
+        w["cand_off"], w["cand"] = synth.candidates(
+            (w["reads"].true_pos // w["B"]).astype(np.int32), nb0, seed=4 + rank)
+    gen_s = time.perf_counter() - t0
+    rs = w["reads"]
+    st = torch.cuda.current_stream()
+    ref = torch.from_numpy(g).cuda()
+    idx = grim.grim_build(ref, w["B"], w["q"], w["max_read_len"], grim.GRIM_LAYOUT_BIN_MAJOR)
+    nb = idx.desc.num_bins
+    dev = dict(reads=torch.from_numpy(rs.seq).cuda(),
+               offsets=torch.from_numpy(rs.offsets.view(np.int64)).cuda(),
+               lens=torch.from_numpy(rs.lens.view(np.int32)).cuda(),
+               e=torch.from_numpy(rs.e.view(np.int16)).cuda(),
+               cand=torch.from_numpy(w["cand"]).cuda(),
+               cand_off=torch.from_numpy(w["cand_off"].view(np.int64)).cuda())
+    n_cand = len(w["cand"])
+    max_e = int(rs.e.max())
+    # autotune the read tile on a sample of the batch
+    ns = min(rs.n, 200_000)
+    cs = int(w["cand_off"][ns])
+    sample = dict(reads=dev["reads"][: int(rs.offsets[ns - 1] + rs.lens[ns - 1])],
+                  offsets=dev["offsets"][:ns], lens=dev["lens"][:ns], e=dev["e"][:ns],
+                  cand=dev["cand"][:cs], cand_off=dev["cand_off"][: ns + 1])
+    tuned = autotune.tune_candidate_unroll(idx, sample, max_e, cache=None)
+    cap = 4 * rs.n + 4096
+    plan = grim.grim_plan_create(idx, max_reads=rs.n, max_bases=len(rs.seq), max_e=max_e, cap=cap,
+                                 max_cand=n_cand, candidates=True, cand_unroll=tuned["unroll"])
+    plan.stage(**dev)
+    torch.cuda.synchronize()
+
+    def step():
+        grim.grim_plan_launch(plan, rs.n, n_cand, st)
+        return grim.grim_plan_wait(plan)
+
+    for _ in range(args.warmup):
+        n_pass = step()
+    if dist:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(st)
+    for _ in range(args.steps):
+        n_pass = step()
+    ev1.record(st)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # the plain single call, with per-kernel timing, on the same inputs
+    ws = grim.Workspace()
+    out = tuple(torch.empty(cap, dtype=dt, device="cuda") for dt in (torch.int32, torch.int32, torch.uint8))
+    grim.grim_filter(idx, **dev, out=out, workspace=ws)
+    grim.grim_profile(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(args.steps):
+        plain = grim.grim_filter(idx, **dev, out=out, workspace=ws)
+    b.record(st)
+    torch.cuda.synchronize()
+    prof = grim.grim_profile_get()
+    grim.grim_profile(False)
+    plain_ms = a.elapsed_time(b) / args.steps
+    assert int(plain[0].numel()) == n_pass
+    k_launch, k_ms = prof.get("candidates", (1, 0.0))
+    kernel_ms = k_ms / max(k_launch, 1)
+    vec_bytes = max(4, 4 ** w["q"] // 8)
+    gbytes = n_cand * (vec_bytes + 4) / 1e9  # one vector gather + its id per pair
+    peaks = {}
+    try:
+        peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    line = {
+        "metric": "reads/s, candidate lists of ragged reads (graph-captured plan)",
+        "value": round(rs.n * world / (ms / 1e3), 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": (f"ragged candidates: {len(g) / 1e9:.1f} Gbp genome, B={w['B']}, "
+                                f"q={w['q']}, bin-major table, {rs.n} reads L in {{100,150,250}} "
+                                f"(.5/.3/.2), e uniform in [0, 0.05 L], {n_cand} candidates "
+                                "(LogNormal median 200, clip 20,000); one graph launch per step"),
+                   "reads": rs.n, "candidates": n_cand, "gen_s": round(gen_s, 1)},
+        "pairs_per_s": round(n_cand * world / (ms / 1e3), 1),
+        "autotune": tuned, "passing_records": n_pass,
+        "plain_grim_filter_ms": round(plain_ms, 3),
+        "plain_reads_per_s": round(rs.n / (plain_ms / 1e3), 1),
+        "roofline": {"bound": "hbm", "kernel": "k_candidates (plain call)",
+                     "kernel_ms": round(kernel_ms, 3),
+                     "achieved": round(gbytes / (kernel_ms / 1e3), 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(gbytes / (kernel_ms / 1e3) / hbm, 4), "traffic": None,
+                     "algorithmic_bytes": round(gbytes * 1e9)},
+    }
+    plan.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "ragged":
+        run_ragged(args, rank, world, local)
     else:
         run_native(args, rank, world, local)
 

@@ -132,6 +132,9 @@ typedef struct {
   uint32_t reserved[7];
 } grim_build_opts;
 
+/* The coarse factor grim_build_ex chooses when opts->coarse_factor is 0. */
+uint32_t grim_default_coarse_factor(uint32_t B, uint32_t q, uint32_t max_read_len);
+
 /* grim_build / grim_build_host with options (opts may be NULL).
  * Errors: as grim_build, and GRIM_E_ARG for an option out of range. */
 int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
@@ -269,7 +272,9 @@ typedef struct {
   uint64_t max_cand;    /* candidate mode: candidates per batch                     */
   uint64_t cap;         /* output records per batch                                 */
   uint32_t flags;       /* GRIM_PLAN_*                                              */
-  uint32_t reserved[7];
+  uint32_t cand_unroll; /* candidate gathers in flight per lane group: 1, 2 or 4;
+                           0 = the library default (tuned by the package's autotuner) */
+  uint32_t reserved[6];
 } grim_plan_desc;
 
 /* Device buffers owned by a plan (layouts as for grim_filter). */

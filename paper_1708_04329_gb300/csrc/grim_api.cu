@@ -146,6 +146,11 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
   return grim_build_ex(ref, len, B, q, max_read_len, layouts, nullptr, stream, out);
 }
 
+uint32_t grim_default_coarse_factor(uint32_t B, uint32_t q, uint32_t max_read_len) {
+  if (B == 0 || q < 2 || q > 6 || max_read_len < q) return 0;
+  return default_coarse_factor(B, q, max_read_len - 1);
+}
+
 int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
                   uint32_t layouts, const grim_build_opts* opts, void* stream, grim_index** out) {
   if (!out) return GRIM_E_ARG;

@@ -53,8 +53,9 @@ struct CandArgs {
 };
 
 constexpr int kWarps = 8;
+constexpr uint32_t kDefaultCandUnroll = 4;
 
-template <int WPB>
+template <int WPB, int U>
 __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
   using C = Cfg<WPB>;
   constexpr int WL = C::WL, G = C::G, CPW = C::CPW;
@@ -120,40 +121,51 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
     const uint32_t K = 32 - __clz(mx);  // planes in use
     const uint32_t thr = ntok - dmax;   // pass iff sum >= (L-q+1) - min(q*e, L-q+1)
 
-    for (uint64_t kb = c0; kb < c1; kb += CPW) {
-      const uint64_t k = kb + slot;
-      const bool valid = k < c1;
-      const uint32_t b = valid ? (uint32_t)__ldg(a.cand + k) : 0u;
-      uint32_t sum = 0;
-      if (valid) {
-        uint32_t v[WL];
-        load_words<WL>(a.ix.bm + (uint64_t)b * WPB + sub * WL, v);
+    // U independent gathers in flight per lane group: load all, then count
+    for (uint64_t kb = c0; kb < c1; kb += (uint64_t)CPW * U) {
+      uint64_t k[U];
+      uint32_t b[U], v[U][WL];
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          if ((uint32_t)p < K) {
-            uint32_t s = 0;
-#pragma unroll
-            for (int w = 0; w < WL; ++w) s += __popc(v[w] & P[p][w]);
-            sum += s << p;
-          }
-        }
+      for (int u = 0; u < U; ++u) {
+        k[u] = kb + (uint64_t)u * CPW + slot;
+        b[u] = k[u] < c1 ? (uint32_t)__ldg(a.cand + k[u]) : 0u;
       }
 #pragma unroll
-      for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-      // bins past num_bins exist only as zero padding of the table (members
-      // of the last super-bin); they never pass
-      const bool real = valid && b < a.ix.num_bins;
-      const bool pass = real && sub == 0 && sum >= thr;
-      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
-      if (bal) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)__popc(bal));
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        if (pass) {
-          const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
-          if (pos < a.rec.cap) {
-            a.rec.keys[pos] = k;
-            a.rec.counts[pos] = (uint8_t)sum;
+      for (int u = 0; u < U; ++u) {
+        if (k[u] < c1) load_words<WL>(a.ix.bm + (uint64_t)b[u] * WPB + sub * WL, v[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const bool valid = k[u] < c1;
+        uint32_t sum = 0;
+        if (valid) {
+#pragma unroll
+          for (int p = 0; p < 8; ++p) {
+            if ((uint32_t)p < K) {
+              uint32_t s = 0;
+#pragma unroll
+              for (int w = 0; w < WL; ++w) s += __popc(v[u][w] & P[p][w]);
+              sum += s << p;
+            }
+          }
+        }
+#pragma unroll
+        for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        // bins past num_bins exist only as zero padding of the table (members
+        // of the last super-bin); they never pass
+        const bool real = valid && b[u] < a.ix.num_bins;
+        const bool pass = real && sub == 0 && sum >= thr;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
+        if (bal) {
+          unsigned long long base = 0;
+          if (lane == 0) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)__popc(bal));
+          base = __shfl_sync(0xFFFFFFFFu, base, 0);
+          if (pass) {
+            const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+            if (pos < a.rec.cap) {
+              a.rec.keys[pos] = k[u];
+              a.rec.counts[pos] = (uint8_t)sum;
+            }
           }
         }
       }
@@ -161,36 +173,44 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
   }
 }
 
-template <int WPB>
-void launch_t(const CandArgs& a, cudaStream_t st, const char* name) {
+template <int WPB, int U>
+void launch_u(const CandArgs& a, cudaStream_t st, const char* name) {
   const uint32_t hist_words = a.ix.r4 >= 4 ? a.ix.r4 / 4 : 1;
   const size_t smem = (size_t)kWarps * hist_words * sizeof(uint32_t);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_candidates<WPB>, kWarps * 32, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_candidates<WPB, U>, kWarps * 32, smem);
   if (per_sm < 1) per_sm = 1;
   uint64_t want = ((uint64_t)a.rv.n_reads + kWarps - 1) / kWarps;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > want) grid = want;
   if (grid < 1) grid = 1;
   ProfScope ps(name, st);
-  k_candidates<WPB><<<(unsigned)grid, kWarps * 32, smem, st>>>(a);
+  k_candidates<WPB, U><<<(unsigned)grid, kWarps * 32, smem, st>>>(a);
+}
+
+template <int WPB>
+void launch_t(const CandArgs& a, cudaStream_t st, const char* name, uint32_t unroll) {
+  if (unroll >= 4) launch_u<WPB, 4>(a, st, name);
+  else if (unroll >= 2) launch_u<WPB, 2>(a, st, name);
+  else launch_u<WPB, 1>(a, st, name);
 }
 
 }  // namespace
 
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
                        const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
-                       const char* prof_name, Live live) {
+                       const char* prof_name, Live live, uint32_t unroll) {
+  if (unroll == 0) unroll = kDefaultCandUnroll;
   if (rv.n_reads == 0) return;
   CandArgs a{ix, rv, cand, cand_off, rec, ctl, live};
   switch (ix.wpb) {
-    case 1: launch_t<1>(a, st, prof_name); break;
-    case 2: launch_t<2>(a, st, prof_name); break;
-    case 8: launch_t<8>(a, st, prof_name); break;
-    case 32: launch_t<32>(a, st, prof_name); break;
-    case 128: launch_t<128>(a, st, prof_name); break;
+    case 1: launch_t<1>(a, st, prof_name, unroll); break;
+    case 2: launch_t<2>(a, st, prof_name, unroll); break;
+    case 8: launch_t<8>(a, st, prof_name, unroll); break;
+    case 32: launch_t<32>(a, st, prof_name, unroll); break;
+    case 128: launch_t<128>(a, st, prof_name, unroll); break;
     default: break;  // q outside 2..6 is rejected by grim_build
   }
 }

@@ -123,9 +123,11 @@ uint32_t exhaustive_tile_bins(uint32_t r4);
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st,
                        const char* prof_name = "exhaustive", Live live = {false, 0});
+// unroll: candidate gathers in flight per lane group (1, 2 or 4; 0 = default)
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
                        const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
-                       const char* prof_name = "candidates", Live live = {false, 0});
+                       const char* prof_name = "candidates", Live live = {false, 0},
+                       uint32_t unroll = 0);
 
 // Radix sort of n (key, count) records by the low key_bits bits of the key,
 // followed by the split into the caller's (read, bin, count) arrays.

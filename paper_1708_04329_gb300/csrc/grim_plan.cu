@@ -115,7 +115,8 @@ int capture(grim_plan* p) {
   if (p->cand_mode) {
     launch_check_candidates(p->buf.cand, p->buf.cand_off, d.max_reads, d.max_cand, v.num_bins,
                             p->ctl, st, live);
-    launch_candidates(v, rv, p->buf.cand, p->buf.cand_off, ra, p->ctl, st, "candidates", live);
+    launch_candidates(v, rv, p->buf.cand, p->buf.cand_off, ra, p->ctl, st, "candidates", live,
+                      d.cand_unroll);
     k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlFinal, 0, 0, 0);
     sort_and_emit(ra, rb, d.cap, bit_length(d.max_cand ? d.max_cand - 1 : 0), ws + L.hist, true,
                   bin_bits, p->buf.cand, p->buf.cand_off, d.max_reads, p->buf.out_read,
@@ -134,7 +135,8 @@ int capture(grim_plan* p) {
                                             &p->ctl->n_surv, p->ctl, kPathCoarse);
       expand_survivors(surv.keys, rcap, cbits, p->f, d.max_reads, icand, ioff, st, p->ctl,
                        kPathCoarse);
-      launch_candidates(v, rv, icand, ioff, ra, p->ctl, st, "candidates_refine", coarse);
+      launch_candidates(v, rv, icand, ioff, ra, p->ctl, st, "candidates_refine", coarse,
+                        d.cand_unroll);
     }
     if (has_exact) {
       const Live exact{true, kPathExact};
@@ -180,7 +182,8 @@ int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_pla
   if (!out) return GRIM_E_ARG;
   *out = nullptr;
   if (!idx || !desc || desc->max_reads == 0 || desc->max_bases == 0) return GRIM_E_ARG;
-  if (desc->cap > 0xFFFFFFFFull || desc->max_e > 0xFFFFu) return GRIM_E_ARG;
+  if (desc->cap > 0xFFFFFFFFull || desc->max_e > 0xFFFFu || desc->cand_unroll > 4)
+    return GRIM_E_ARG;
   const bool cand_mode = (desc->flags & GRIM_PLAN_CANDIDATES) != 0;
   if (cand_mode && !(idx->layouts & GRIM_LAYOUT_BIN_MAJOR)) return GRIM_E_NO_LAYOUT;
   if (!cand_mode && !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR) && !two_level_capable(idx))

@@ -43,7 +43,7 @@ EXPORTS = (
     "grim_loc_to_bin", "grim_edits_for_rate", "grim_profile", "grim_profile_get",
     "grim_filter_noalloc", "grim_last_filter_stats", "grim_build_ex", "grim_build_host_ex",
     "grim_plan_create", "grim_plan_buffers_get", "grim_plan_launch", "grim_plan_query",
-    "grim_plan_wait", "grim_plan_device_bytes", "grim_plan_free",
+    "grim_plan_wait", "grim_plan_device_bytes", "grim_plan_free", "grim_default_coarse_factor",
 )
 
 
@@ -80,7 +80,7 @@ class _BuildOpts(C.Structure):
 class _PlanDesc(C.Structure):
     _fields_ = [("max_reads", C.c_uint32), ("max_e", C.c_uint32), ("max_bases", C.c_uint64),
                 ("max_cand", C.c_uint64), ("cap", C.c_uint64), ("flags", C.c_uint32),
-                ("reserved", C.c_uint32 * 7)]
+                ("cand_unroll", C.c_uint32), ("reserved", C.c_uint32 * 6)]
 
 
 class _PlanBuffers(C.Structure):
@@ -112,6 +112,8 @@ def _lib() -> C.CDLL:
         lib.grim_build_host_ex.restype = i32
         lib.grim_build_host_ex.argtypes = [vp, u64, u32, u32, u32, u32, C.POINTER(_BuildOpts), vp,
                                            pp]
+        lib.grim_default_coarse_factor.restype = u32
+        lib.grim_default_coarse_factor.argtypes = [u32, u32, u32]
         lib.grim_index_info.restype = i32
         lib.grim_index_info.argtypes = [vp, C.POINTER(_Desc)]
         lib.grim_free.restype = None
@@ -349,6 +351,10 @@ def grim_build_host_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GR
     if rc != GRIM_OK:
         raise GrimError(rc, "grim_build_host_ex")
     return GrimIndex(h.value)
+
+
+def grim_default_coarse_factor(B: int, q: int, max_read_len: int) -> int:
+    return int(_lib().grim_default_coarse_factor(B, q, max_read_len))
 
 
 def grim_index_info(index: GrimIndex) -> IndexDesc:
@@ -610,9 +616,9 @@ class GrimPlan:
 
 
 def grim_plan_create(index: GrimIndex, max_reads: int, max_bases: int, max_e: int, cap: int,
-                     max_cand: int = 0, candidates: bool = False) -> GrimPlan:
+                     max_cand: int = 0, candidates: bool = False, cand_unroll: int = 0) -> GrimPlan:
     d = _PlanDesc(max_reads, max_e, max_bases, max_cand, cap,
-                  GRIM_PLAN_CANDIDATES if candidates else 0)
+                  GRIM_PLAN_CANDIDATES if candidates else 0, cand_unroll)
     h = C.c_void_p()
     rc = _lib().grim_plan_create(index.handle, C.byref(d), C.byref(h))
     if rc != GRIM_OK:

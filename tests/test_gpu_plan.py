@@ -104,3 +104,35 @@ def test_plan_equals_filter_and_reports_errors(world):
     assert grim.grim_plan_device_bytes(plan2) > 0
     with pytest.raises(grim.GrimError):
         grim.grim_plan_launch(plan2, 401)
+
+
+def test_ragged_candidates_sampled_parity():
+    """The ragged candidate workload at 200 Mbp / 200k reads (~66M pairs) in one
+    plan launch; the oracle checks the first 3,000 reads' lists exactly."""
+    from paper_1708_04329_gb300 import autotune, grim, synth
+
+    w = synth.ragged_candidates(n_reads=200_000, n=200_000_000)
+    rs, off, cand = w["reads"], w["cand_off"], w["cand"]
+    idx = build(w["genome"], w["B"], w["q"], w["max_read_len"], 2)
+    kw = dev_reads(rs)
+    kw["cand"] = torch.from_numpy(cand).cuda()
+    kw["cand_off"] = torch.from_numpy(off.view(np.int64)).cuda()
+    ns = 20_000
+    cs = int(off[ns])
+    sample = dict(reads=kw["reads"][: int(rs.offsets[ns - 1] + rs.lens[ns - 1])],
+                  offsets=kw["offsets"][:ns], lens=kw["lens"][:ns], e=kw["e"][:ns],
+                  cand=kw["cand"][:cs], cand_off=kw["cand_off"][: ns + 1])
+    tuned = autotune.tune_candidate_unroll(idx, sample, int(rs.e.max()), cache=None)
+    assert tuned["unroll"] in (1, 2, 4)
+    plan = grim.grim_plan_create(idx, max_reads=rs.n, max_bases=len(rs.seq), max_e=int(rs.e.max()),
+                                 cap=4 * rs.n, max_cand=len(cand), candidates=True,
+                                 cand_unroll=tuned["unroll"])
+    r, b, c = (_host(x) for x in plan.run(**kw))
+    k = 3000
+    sub = rs.subset(range(k))
+    want = oracle.filter(oracle.bin_vectors(w["genome"], w["B"], w["q"], w["max_read_len"]), sub,
+                         cand_off=off[: k + 1], cand=cand[: int(off[k])])
+    sel = r < k
+    assert_same((r[sel], b[sel], c[sel]), want)
+    # every read passes its true bin (planted edits <= e)
+    assert set(zip(r.tolist(), b.tolist())) >= {(i, int(rs.true_pos[i]) // w["B"]) for i in range(rs.n)}
