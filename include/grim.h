@@ -272,7 +272,7 @@ typedef struct {
   uint64_t max_cand;    /* candidate mode: candidates per batch                     */
   uint64_t cap;         /* output records per batch                                 */
   uint32_t flags;       /* GRIM_PLAN_*                                              */
-  uint32_t cand_unroll; /* candidate gathers in flight per lane group: 1, 2 or 4;
+  uint32_t cand_unroll; /* candidate gathers in flight per lane group: 1, 2, 4 or 8;
                            0 = the library default (tuned by the package's autotuner) */
   uint32_t reserved[6];
 } grim_plan_desc;

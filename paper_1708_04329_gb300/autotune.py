@@ -7,7 +7,7 @@ caller's reads with CUDA events:
   of the coarse table).  Candidates are the power-of-two neighbours of the
   presence-model default; each needs its own index build (~0.1 s at 3.1 Gbp).
 * the read tile of the candidate mode: how many candidate gathers each lane
-  group keeps in flight (1, 2 or 4), timed through graph-captured plans.
+  group keeps in flight (1, 2, 4 or 8), timed through graph-captured plans.
 
 Results are cached in a JSON file keyed by the problem's shape and the GPU,
 so a service tunes once per (reference, parameters, device).
@@ -97,7 +97,7 @@ def tune_coarse_factor(ref, B: int, q: int, max_read_len: int, sample: dict,
     return out
 
 
-def tune_candidate_unroll(index, sample: dict, max_e: int, unrolls=(1, 2, 4), repeats: int = 3,
+def tune_candidate_unroll(index, sample: dict, max_e: int, unrolls=(1, 2, 4, 8), repeats: int = 3,
                           cache: Path | None = DEFAULT_CACHE) -> dict:
     """Pick the number of candidate gathers in flight per lane group.
 

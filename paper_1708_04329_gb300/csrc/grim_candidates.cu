@@ -78,7 +78,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
     const uint64_t c0 = a.cand_off[r], c1 = a.cand_off[r + 1];
     if (c0 == c1) continue;
 
-    // multiplicity histogram of the read's clean tokens
+    // multiplicity histogram of the read's clean tokens (the warp has
+    // finished reading the previous read's histogram)
+    __syncwarp();
     for (uint32_t i = lane; i < hist_words; i += 32) hist[i] = 0;
     __syncwarp();
     const uint32_t m = a.rv.meta[r];
@@ -90,35 +92,37 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
     }
     __syncwarp();
 
-    // bit planes of the multiplicities for this lane's WL words
-    uint32_t P[8][WL];
+    // the largest multiplicity decides how many bit planes the sums need
+    // (almost always 1 or 2)
     uint32_t mx = 0;
-#pragma unroll
-    for (int w = 0; w < WL; ++w) {
-      const uint32_t wi = sub * WL + w;  // word index in the vector: tokens wi*32 .. wi*32+31
-      uint32_t hw[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint32_t h = wi * 8 + j;
-        hw[j] = h < hist_words && (wi * 32 + 4 * j) < r4 ? hist[h] : 0u;
-        mx = max(mx, max(max(hw[j] & 0xFFu, (hw[j] >> 8) & 0xFFu),
-                         max((hw[j] >> 16) & 0xFFu, hw[j] >> 24)));
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        uint32_t pw = 0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          uint32_t x = (hw[j] >> k) & 0x01010101u;  // bit k of 4 byte counters
-          x |= x >> 7;
-          x |= x >> 14;
-          pw |= (x & 0xFu) << (4 * j);
-        }
-        P[k][w] = pw;
-      }
+    for (uint32_t i = lane; i < hist_words; i += 32) {
+      const uint32_t h = hist[i];
+      mx = max(mx, max(max(h & 0xFFu, (h >> 8) & 0xFFu), max((h >> 16) & 0xFFu, h >> 24)));
     }
     mx = __reduce_max_sync(0xFFFFFFFFu, mx);
     const uint32_t K = 32 - __clz(mx);  // planes in use
+    // bit planes k < K of the multiplicities for this lane's WL words
+    uint32_t P[8][WL];
+#pragma unroll
+    for (int w = 0; w < WL; ++w) {
+      const uint32_t wi = sub * WL + w;  // word index in the vector: tokens wi*32 .. wi*32+31
+#pragma unroll
+      for (int k = 0; k < 8; ++k) P[k][w] = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint32_t h = wi * 8 + j;
+        const uint32_t hw = h < hist_words && (wi * 32 + 4 * j) < r4 ? hist[h] : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if ((uint32_t)k < K) {
+            uint32_t x = (hw >> k) & 0x01010101u;  // bit k of 4 byte counters
+            x |= x >> 7;
+            x |= x >> 14;
+            P[k][w] |= (x & 0xFu) << (4 * j);
+          }
+        }
+      }
+    }
     const uint32_t thr = ntok - dmax;   // pass iff sum >= (L-q+1) - min(q*e, L-q+1)
 
     // U independent gathers in flight per lane group: load all, then count
@@ -192,7 +196,8 @@ void launch_u(const CandArgs& a, cudaStream_t st, const char* name) {
 
 template <int WPB>
 void launch_t(const CandArgs& a, cudaStream_t st, const char* name, uint32_t unroll) {
-  if (unroll >= 4) launch_u<WPB, 4>(a, st, name);
+  if (unroll >= 8) launch_u<WPB, 8>(a, st, name);
+  else if (unroll >= 4) launch_u<WPB, 4>(a, st, name);
   else if (unroll >= 2) launch_u<WPB, 2>(a, st, name);
   else launch_u<WPB, 1>(a, st, name);
 }

@@ -23,11 +23,11 @@ constexpr uint32_t kSortTile = kSortThreads * kSortItems;
 // gate (ctl, path) makes the kernel a no-op unless the batch took that path.
 __device__ __forceinline__ uint64_t live_n(const unsigned long long* n_live, uint64_t n) {
   if (!n_live) return n;
-  const uint64_t v = *reinterpret_cast<const volatile unsigned long long*>(n_live);
+  const uint64_t v = *n_live;
   return v < n ? v : n;
 }
 __device__ __forceinline__ bool gate_off(const Ctl* c, uint32_t gate) {
-  return c && gate && *reinterpret_cast<const volatile uint32_t*>(&c->path) != gate;
+  return c && gate && c->path != gate;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const unsigned long long* __restrict__ keys,
@@ -140,7 +140,7 @@ __global__ void k_emit(const unsigned long long* __restrict__ keys,
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (gate_off(gc, gate)) return;
   if (i >= live_n(n_live, n)) return;
-  if (n_reads_live) n_reads = *reinterpret_cast<const volatile uint32_t*>(n_reads_live);
+  if (n_reads_live) n_reads = *n_reads_live;
   const unsigned long long key = keys[i];
   uint32_t r, b;
   if (cand_mode) {
@@ -172,8 +172,8 @@ __global__ void k_expand(const unsigned long long* __restrict__ keys, uint64_t n
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (lc) {
     if (gate_off(lc, gate)) return;
-    n_surv = *reinterpret_cast<const volatile unsigned long long*>(&lc->n_surv);
-    n_reads = *reinterpret_cast<const volatile uint32_t*>(&lc->live_reads);
+    n_surv = lc->n_surv;
+    n_reads = lc->live_reads;
   }
   const unsigned long long mask = cbits >= 64 ? ~0ull : ((1ull << cbits) - 1ull);
   if (i < n_surv) {

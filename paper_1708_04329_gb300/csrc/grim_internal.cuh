@@ -48,11 +48,13 @@ struct Live {
   bool on;
   uint32_t gate;
 };
+// (plain loads: the fields are written by earlier kernels of the stream and
+// do not change while the reading kernel runs)
 __device__ __forceinline__ uint32_t live_reads(const Ctl* c, const Live& l, uint32_t host_n) {
-  return l.on ? *reinterpret_cast<const volatile uint32_t*>(&c->live_reads) : host_n;
+  return l.on ? c->live_reads : host_n;
 }
 __device__ __forceinline__ bool gated_off(const Ctl* c, const Live& l) {
-  return l.on && l.gate && *reinterpret_cast<const volatile uint32_t*>(&c->path) != l.gate;
+  return l.on && l.gate && c->path != l.gate;
 }
 
 constexpr uint32_t kStatusShort = 1u;     // read with L < q
@@ -123,7 +125,7 @@ uint32_t exhaustive_tile_bins(uint32_t r4);
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st,
                        const char* prof_name = "exhaustive", Live live = {false, 0});
-// unroll: candidate gathers in flight per lane group (1, 2 or 4; 0 = default)
+// unroll: candidate gathers in flight per lane group (1, 2, 4 or 8; 0 = default)
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
                        const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
                        const char* prof_name = "candidates", Live live = {false, 0},

@@ -182,7 +182,7 @@ int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_pla
   if (!out) return GRIM_E_ARG;
   *out = nullptr;
   if (!idx || !desc || desc->max_reads == 0 || desc->max_bases == 0) return GRIM_E_ARG;
-  if (desc->cap > 0xFFFFFFFFull || desc->max_e > 0xFFFFu || desc->cand_unroll > 4)
+  if (desc->cap > 0xFFFFFFFFull || desc->max_e > 0xFFFFu || desc->cand_unroll > 8)
     return GRIM_E_ARG;
   const bool cand_mode = (desc->flags & GRIM_PLAN_CANDIDATES) != 0;
   if (cand_mode && !(idx->layouts & GRIM_LAYOUT_BIN_MAJOR)) return GRIM_E_NO_LAYOUT;

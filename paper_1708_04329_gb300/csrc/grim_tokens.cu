@@ -52,16 +52,23 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
       v = (v << 2) | (((u >> 1) ^ (u >> 2)) & 3u);  // A0 C1 G2 T3
     }
     const uint32_t row = clean ? v : rowInvalid(r4);
+    if (!presence) {  // no order wanted (candidate lists): positions as they are
+      out[j] = (uint16_t)row;
+      continue;
+    }
     s_row[warp][j] = (uint16_t)row;
-    const unsigned long long rare = !presence ? 0ull : clean ? (unsigned long long)presence[row] + 1 : 0ull;
+    const unsigned long long rare = clean ? (unsigned long long)presence[row] + 1 : 0ull;
     s_key[warp][j] = (rare << 8) | j;
   }
   __syncwarp();
-  for (uint32_t j = lane; j < ntok; j += 32) {
-    const unsigned long long mine = s_key[warp][j];
-    uint32_t rank = 0;
-    for (uint32_t i = 0; i < ntok; ++i) rank += s_key[warp][i] < mine;
-    out[rank] = s_row[warp][j];
+  if (presence) {
+    // rank = number of smaller keys (keys are distinct: position breaks ties)
+    for (uint32_t j = lane; j < ntok; j += 32) {
+      const unsigned long long mine = s_key[warp][j];
+      uint32_t rank = 0;
+      for (uint32_t i = 0; i < ntok; ++i) rank += s_key[warp][i] < mine;
+      out[rank] = s_row[warp][j];
+    }
   }
   for (uint32_t j = ntok + lane; j < ts; j += 32) out[j] = (uint16_t)rowPad(r4);
   if (lane == 0) {
@@ -81,8 +88,8 @@ __global__ void k_check_candidates(const int32_t* __restrict__ cand,
                                    uint64_t n_cand, uint64_t num_bins, Ctl* ctl, Live live) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (live.on) {
-    n_reads = *reinterpret_cast<volatile uint32_t*>(&ctl->live_reads);
-    n_cand = *reinterpret_cast<volatile unsigned long long*>(&ctl->live_cand);
+    n_reads = ctl->live_reads;
+    n_cand = ctl->live_cand;
   }
   if (i < n_cand) {
     int32_t b = cand[i];

@@ -123,7 +123,7 @@ def test_ragged_candidates_sampled_parity():
                   offsets=kw["offsets"][:ns], lens=kw["lens"][:ns], e=kw["e"][:ns],
                   cand=kw["cand"][:cs], cand_off=kw["cand_off"][: ns + 1])
     tuned = autotune.tune_candidate_unroll(idx, sample, int(rs.e.max()), cache=None)
-    assert tuned["unroll"] in (1, 2, 4)
+    assert tuned["unroll"] in (1, 2, 4, 8)
     plan = grim.grim_plan_create(idx, max_reads=rs.n, max_bases=len(rs.seq), max_e=int(rs.e.max()),
                                  cap=4 * rs.n, max_cand=len(cand), candidates=True,
                                  cand_unroll=tuned["unroll"])
