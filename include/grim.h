@@ -49,7 +49,10 @@ extern "C" {
 #define GRIM_E_WORKSPACE (-9)      /* workspace smaller than grim_filter_workspace_size()       */
 #define GRIM_E_NO_LAYOUT (-10)     /* the index lacks the table layout this call needs          */
 #define GRIM_E_UNSUPPORTED (-11)   /* parameter outside what this build implements              */
-#define GRIM_E_NOT_READY (-12)     /* grim_plan_query: the plan's last launch is still running  */
+#define GRIM_E_NOT_READY (-12)     /* a plan launch or server request has not finished yet     */
+#define GRIM_E_BUSY (-13)          /* grim_server_submit: the server's queue is full            */
+#define GRIM_E_IO (-14)            /* a file could not be opened, read or written               */
+#define GRIM_E_FORMAT (-15)        /* not an index file of this library, or damaged             */
 
 /* ---- table layouts (bit mask for grim_build) ----------------------------- */
 /* Token-major: row t holds token t's bit for every bin, contiguous
@@ -145,6 +148,25 @@ int grim_build_host_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q,
 
 /* Fill *out with the index's sizes and device table pointers. */
 int grim_index_info(const grim_index* idx, grim_index_desc* out);
+
+/*
+ * Index persistence (§GRIM-Filter: the bit vectors are generated once per
+ * reference and stored for later runs).  grim_save writes the build
+ * parameters and every table the index holds to `path` (a 256-byte header,
+ * then the tables exactly as in device memory, with a checksum); grim_load
+ * reads such a file into new device tables on the current device.
+ *   layouts  the tables to load (a subset of those in the file), 0 = all
+ *   flags    GRIM_LOAD_VERIFY: recompute the checksum while reading
+ * A loaded index is identical to the one saved (same parameters, coarse
+ * factor and table bits) and gives identical filter results.  Both calls
+ * synchronise.  Errors: GRIM_E_ARG, GRIM_E_IO (open/read/write failed),
+ * GRIM_E_FORMAT (bad magic, version, sizes or checksum; truncated file),
+ * GRIM_E_NO_LAYOUT (a requested table is not in the file), GRIM_E_NOMEM,
+ * GRIM_E_CUDA.
+ */
+#define GRIM_LOAD_VERIFY 1u
+int grim_save(const grim_index* idx, const char* path);
+int grim_load(const char* path, uint32_t layouts, uint32_t flags, grim_index** out);
 
 /* Release an index and its device tables (NULL is ignored). */
 void grim_free(grim_index* idx);
@@ -263,6 +285,14 @@ int grim_filter_noalloc(const grim_index* idx, const char* reads, const uint64_t
 typedef struct grim_plan grim_plan;
 
 #define GRIM_PLAN_CANDIDATES 1u /* candidate-list mode (else all bins) */
+/* Host-memory plan: the buffers of grim_plan_buffers_get are mapped pinned
+ * HOST memory.  The caller writes a batch's inputs there; the graph copies
+ * them to the device itself (only the bytes the batch uses: reads up to the
+ * largest offset + length, which grim_plan_launch checks against max_bases)
+ * and writes the pass list straight back into the host output buffers, so a
+ * batch costs one graph launch and no separate copies.  Inputs and outputs
+ * must not be touched while a launch of the plan is in flight. */
+#define GRIM_PLAN_HOST_IO 2u
 
 typedef struct {
   uint32_t max_reads;   /* reads per batch, >= 1                                    */
@@ -277,7 +307,8 @@ typedef struct {
   uint32_t reserved[6];
 } grim_plan_desc;
 
-/* Device buffers owned by a plan (layouts as for grim_filter). */
+/* Buffers owned by a plan (layouts as for grim_filter): device memory, or
+ * mapped pinned host memory for a GRIM_PLAN_HOST_IO plan. */
 typedef struct {
   char* reads;          /* [max_bases]                                 */
   uint64_t* offsets;    /* [max_reads]                                 */
@@ -292,11 +323,14 @@ typedef struct {
 
 /* Allocate a plan's buffers (cudaMalloc, pinned host memory) and capture its
  * graph.  The index must outlive the plan.
- * Errors: GRIM_E_ARG, GRIM_E_NO_LAYOUT, GRIM_E_NOMEM, GRIM_E_CUDA. */
+ * Errors: GRIM_E_ARG (zero maxima, unknown flags, cand_unroll > 8),
+ * GRIM_E_NO_LAYOUT, GRIM_E_NOMEM, GRIM_E_CUDA. */
 int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_plan** out);
 int grim_plan_buffers_get(const grim_plan* plan, grim_plan_buffers* out);
 /* Enqueue one run on `stream` for a batch of n_reads reads (and n_cand
- * candidates) already in the plan's buffers.  Asynchronous. */
+ * candidates) already in the plan's buffers.  Asynchronous.  A read ending
+ * past max_bases fails the batch with GRIM_E_ARG (a host-memory plan refuses
+ * the launch with GRIM_E_ARG instead). */
 int grim_plan_launch(grim_plan* plan, uint32_t n_reads, uint64_t n_cand, void* stream);
 /* GRIM_OK if the last launch has finished (or none was made),
  * GRIM_E_NOT_READY if it is still running. */
@@ -307,6 +341,98 @@ int grim_plan_wait(grim_plan* plan, uint64_t* n_out);
 /* Device bytes the plan holds (inputs, outputs and workspace). */
 uint64_t grim_plan_device_bytes(const grim_plan* plan);
 void grim_plan_free(grim_plan* plan);
+
+/* ---- serving: continuous batching over a resident index ---------------- */
+/*
+ * A server keeps an index resident and filters requests -- read batches of
+ * any size, read lengths and per-read edit budgets (and, in candidate mode,
+ * candidate lists) -- as they arrive.  The paper filters each read on its
+ * own (§GRIM-Filter, Fig. 5); a server is this library's way of feeding
+ * many independent callers to the device at once, and has no counterpart
+ * in the paper.
+ *
+ * A scheduler thread owns `slots` host-memory plans (GRIM_PLAN_HOST_IO), each
+ * on its own stream.  Whenever a slot is free it merges the queued requests,
+ * oldest first, into one batch within the slot's limits (max_reads,
+ * max_bases, max_cand) and launches it; requests that arrive meanwhile wait
+ * for the next free slot, and the batches of different slots overlap on the
+ * device.  The slots' device memory (batch buffers, workspace, pass lists)
+ * is bounded by mem_budget.  A request's result is the same as grim_filter
+ * of that request alone: the filter works read by read, and each request's
+ * records are handed back with its own read numbering.  A merged batch whose
+ * pass list exceeds `cap` is split and its requests rerun one per batch; a
+ * request alone over `cap` completes with GRIM_E_OVERFLOW.
+ *
+ * Requests are validated at submission (read lengths against the index,
+ * e <= max_e, sizes against the slot limits, candidate ids and offsets), so
+ * one bad request cannot fail the batch it would have joined.
+ */
+typedef struct grim_server grim_server;
+
+typedef struct {
+  uint32_t slots;            /* batches in flight on the device, >= 1 (reduced to fit mem_budget) */
+  uint32_t max_reads;        /* reads per merged batch, >= 1; a larger request is refused */
+  uint64_t max_bases;        /* read bytes per merged batch, >= 1 */
+  uint64_t max_cand;         /* candidate mode: candidates per merged batch                */
+  uint64_t cap;              /* pass-list records per merged batch, >= 1                   */
+  uint32_t max_e;            /* largest per-read edit budget a request may carry          */
+  uint32_t flags;            /* GRIM_PLAN_CANDIDATES, or 0 for all bins                    */
+  uint64_t mem_budget;       /* device bytes the slots may hold together (0: no limit)     */
+  uint64_t max_queued_reads; /* submit returns GRIM_E_BUSY past this many waiting reads
+                                (0: no limit; a request is always taken into an empty queue) */
+  uint32_t cand_unroll;      /* as grim_plan_desc                                          */
+  uint32_t reserved[7];
+} grim_server_desc;
+
+typedef struct {
+  int32_t status;           /* GRIM_OK or the request's error                        */
+  uint32_t n_reads;
+  uint64_t n_out;           /* passing records (the total, on GRIM_E_OVERFLOW)       */
+  uint64_t batch;           /* sequence number (from 1) of the batch that served it  */
+  uint32_t batch_requests;  /* requests merged into that batch                       */
+  uint32_t batch_reads;     /* reads in that batch                                   */
+  uint64_t t_submit_ns;     /* steady-clock times: submission, launch, completion    */
+  uint64_t t_launch_ns;
+  uint64_t t_done_ns;
+} grim_request_info;
+
+typedef struct {
+  uint32_t slots;           /* slots created (after the memory budget)   */
+  uint32_t reserved;
+  uint64_t device_bytes;    /* device bytes the slots hold                */
+  uint64_t submitted, completed, batches, batch_reads, reads_done, records;
+  uint64_t overflow_splits; /* merged batches rerun one request at a time */
+  uint64_t queued_requests, queued_reads;
+} grim_server_stats;
+
+/* Create the slots' plans and start the scheduler.  The index must outlive
+ * the server.  Errors: GRIM_E_ARG, GRIM_E_NO_LAYOUT, GRIM_E_NOMEM (not even
+ * one slot fits mem_budget), GRIM_E_CUDA. */
+int grim_server_create(const grim_index* idx, const grim_server_desc* desc, grim_server** out);
+/* Queue a request; every pointer is HOST memory and is copied before the
+ * call returns.  reads/offsets/lens/e as grim_filter; cand/cand_off (CSR
+ * from 0) in candidate mode, both NULL in all-bins mode.  *ticket names the
+ * request.  Errors: GRIM_E_ARG, GRIM_E_READ_TOO_SHORT, GRIM_E_READ_TOO_LONG,
+ * GRIM_E_BAD_CANDIDATE, GRIM_E_BUSY (queue full), GRIM_E_NOMEM, or the CUDA
+ * failure that stopped the server. */
+int grim_server_submit(grim_server* s, const char* reads, const uint64_t* offsets,
+                       const uint32_t* lens, uint32_t n_reads, const uint16_t* e,
+                       const int32_t* cand, const uint64_t* cand_off, uint64_t* ticket);
+/* Block until the request has completed (timeout_us < 0: no limit).
+ * GRIM_OK when it has, GRIM_E_NOT_READY on timeout, GRIM_E_ARG for an
+ * unknown ticket. */
+int grim_server_wait(grim_server* s, uint64_t ticket, int64_t timeout_us);
+/* Copy a completed request's pass list (sorted by read, then bin or
+ * candidate order) into host buffers of `cap` records and release it.
+ * `info` (may be NULL) receives its status, sizes and times.
+ * GRIM_E_NOT_READY: still running.  GRIM_E_OVERFLOW: cap < info->n_out; the
+ * request is kept, take again with more room.  A failed request returns its
+ * error and is released. */
+int grim_server_take(grim_server* s, uint64_t ticket, uint32_t* out_read, uint32_t* out_bin,
+                     uint8_t* out_count, uint64_t cap, grim_request_info* info);
+int grim_server_stats_get(grim_server* s, grim_server_stats* out);
+/* Drop queued requests, let batches on the device finish, stop, release. */
+void grim_server_free(grim_server* s);
 
 /* ---- helpers of the mapper around the filter (§GRIM-Filter, Fig. 5) ----- */
 

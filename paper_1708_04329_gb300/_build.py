@@ -30,6 +30,8 @@ GRIM_SOURCES = [
     "grim_compact.cu",
     "grim_noalloc.cu",
     "grim_plan.cu",
+    "grim_serve.cu",
+    "grim_io.cu",
 ]
 GRIM_HEADERS = ["grim_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -89,7 +91,8 @@ def build_grim(force: bool = False, extra: list[str] | None = None) -> Path:
             list(ex.map(_run, jobs))
     if force or jobs or _stale(out, objs):
         tmp = out.with_suffix(f".so.tmp{os.getpid()}")
-        _run([nvcc] + ARCH + ["-shared", "--cudart", "static", "-o", str(tmp)] + [str(o) for o in objs])
+        _run([nvcc] + ARCH + ["-shared", "--cudart", "static", "-o", str(tmp)] + [str(o) for o in objs]
+             + ["-lpthread"])
         os.replace(tmp, out)
     return out
 

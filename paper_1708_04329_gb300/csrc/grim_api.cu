@@ -74,6 +74,78 @@ cudaEvent_t take_event() {
 
 }  // namespace
 
+// Validate an index's parameters and allocate its tables (contents not yet
+// written): token-major [4^q][num_bins_pad/32], bin-major padded with zero
+// vectors to whole super-bins, coarse token-major over super-bins of f bins,
+// and the per-token presence counts.
+int index_alloc(uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len, uint32_t layouts,
+                uint32_t f, grim_index** out) {
+  *out = nullptr;
+  if (f == 0 || f > 64) return GRIM_E_ARG;
+  if (len == 0 || B == 0 || max_read_len < q || layouts == 0 || (layouts & ~GRIM_LAYOUT_ALL))
+    return GRIM_E_ARG;
+  if (q < 2 || q > 6 || max_read_len - q + 1 > kMaxTokens) return GRIM_E_UNSUPPORTED;
+  IndexView v{};
+  v.n = len;
+  v.B = B;
+  v.q = q;
+  v.ext = max_read_len - 1;
+  v.max_read_len = max_read_len;
+  v.r4 = 1u << (2 * q);
+  v.wpb = v.r4 >= 32 ? v.r4 / 32 : 1;
+  v.num_bins = (len + B - 1) / B;
+  v.num_bins_pad = (v.num_bins + kTileBins - 1) / kTileBins * kTileBins;
+  v.wpad = v.num_bins_pad / 32;
+  if (v.num_bins > 0xFFFFFFFFull) return GRIM_E_UNSUPPORTED;  // bins are uint32 in the output
+  // super-bins: core f*B, the same extension (window = union of f bins' windows)
+  IndexView cv = v;
+  cv.B = v.B * f;
+  cv.num_bins = (len + cv.B - 1) / cv.B;
+  cv.num_bins_pad = (cv.num_bins + kTileBins - 1) / kTileBins * kTileBins;
+  cv.wpad = cv.num_bins_pad / 32;
+  // bin-major vectors padded with zero vectors to whole super-bins
+  const uint64_t bm_bins = cv.num_bins * f;
+
+  grim_index* ix = new (std::nothrow) grim_index{};
+  if (!ix) return GRIM_E_NOMEM;
+  ix->layouts = layouts;
+  ix->factor = f;
+  auto fail = [&](cudaError_t e) {
+    grim_free(ix);
+    return cuda_fail(e);
+  };
+  cudaError_t e;
+  if (layouts & GRIM_LAYOUT_TOKEN_MAJOR) {
+    e = cudaMalloc(&ix->tm, (uint64_t)v.r4 * v.wpad * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(e);
+  }
+  if (layouts & GRIM_LAYOUT_BIN_MAJOR) {
+    e = cudaMalloc(&ix->bm, bm_bins * v.wpb * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(e);
+  }
+  if (layouts & GRIM_LAYOUT_COARSE) {
+    e = cudaMalloc(&ix->ctm, (uint64_t)cv.r4 * cv.wpad * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(e);
+  }
+  if (layouts & (GRIM_LAYOUT_COARSE | GRIM_LAYOUT_TOKEN_MAJOR)) {
+    e = cudaMalloc(&ix->presence, (uint64_t)v.r4 * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(e);
+  }
+  v.tm = ix->tm;
+  v.bm = ix->bm;
+  v.presence = ix->presence;
+  ix->v = v;
+  cv.tm = ix->ctm;
+  cv.bm = nullptr;
+  cv.presence = ix->presence;
+  ix->cv = cv;
+  *out = ix;
+  return GRIM_OK;
+}
+
+int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+
+
 void prof_suspend(bool on) { g_prof_suspended = on; }
 
 ProfScope::ProfScope(const char* name, cudaStream_t s) : slot(-1), st(s) {
@@ -134,7 +206,10 @@ const char* grim_strerror(int s) {
     case GRIM_E_WORKSPACE: return "workspace too small";
     case GRIM_E_NO_LAYOUT: return "index lacks the table layout this call needs";
     case GRIM_E_UNSUPPORTED: return "parameter outside what this build implements";
-    case GRIM_E_NOT_READY: return "the plan's last launch is still running";
+    case GRIM_E_NOT_READY: return "not finished yet";
+    case GRIM_E_BUSY: return "the server's queue is full";
+    case GRIM_E_IO: return "file could not be opened, read or written";
+    case GRIM_E_FORMAT: return "not an index file of this library, or damaged";
     default: return "unknown status";
   }
 }
@@ -155,74 +230,22 @@ int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_
                   uint32_t layouts, const grim_build_opts* opts, void* stream, grim_index** out) {
   if (!out) return GRIM_E_ARG;
   *out = nullptr;
-  const uint32_t f = (opts && opts->coarse_factor)
-                         ? opts->coarse_factor
-                         : default_coarse_factor(B, q, max_read_len - 1);
-  if (f > 64) return GRIM_E_ARG;
-  if (!ref || len == 0 || B == 0 || max_read_len < q || layouts == 0 ||
-      (layouts & ~GRIM_LAYOUT_ALL))
-    return GRIM_E_ARG;
-  if (q < 2 || q > 6 || max_read_len - q + 1 > kMaxTokens) return GRIM_E_UNSUPPORTED;
+  if (!ref || B == 0 || max_read_len < q) return GRIM_E_ARG;
+  const uint32_t f = (opts && opts->coarse_factor) ? opts->coarse_factor
+                     : (q >= 2 && q <= 6)              ? default_coarse_factor(B, q, max_read_len - 1)
+                                                       : 2u;  // q is refused by index_alloc
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  IndexView v{};
-  v.n = len;
-  v.B = B;
-  v.q = q;
-  v.ext = max_read_len - 1;
-  v.max_read_len = max_read_len;
-  v.r4 = 1u << (2 * q);
-  v.wpb = v.r4 >= 32 ? v.r4 / 32 : 1;
-  v.num_bins = (len + B - 1) / B;
-  v.num_bins_pad = (v.num_bins + kTileBins - 1) / kTileBins * kTileBins;
-  v.wpad = v.num_bins_pad / 32;
-  if (v.num_bins > 0xFFFFFFFFull) return GRIM_E_UNSUPPORTED;  // bins are uint32 in the output
-  // super-bins: core f*B, the same extension (window = union of f bins' windows)
-  IndexView cv = v;
-  cv.B = v.B * f;
-  cv.num_bins = (len + cv.B - 1) / cv.B;
-  cv.num_bins_pad = (cv.num_bins + kTileBins - 1) / kTileBins * kTileBins;
-  cv.wpad = cv.num_bins_pad / 32;
-  // bin-major vectors padded with zero vectors to whole super-bins
+  grim_index* ix = nullptr;
+  const int rc = index_alloc(len, B, q, max_read_len, layouts, f, &ix);
+  if (rc != GRIM_OK) return rc;
+  const IndexView& v = ix->v;
+  const IndexView& cv = ix->cv;
   const uint64_t bm_bins = cv.num_bins * f;
-
-  grim_index* ix = new (std::nothrow) grim_index{};
-  if (!ix) return GRIM_E_NOMEM;
-  ix->layouts = layouts;
-  ix->factor = f;
   auto fail = [&](int code) {
-    cudaFree(ix->tm);
-    cudaFree(ix->bm);
-    cudaFree(ix->ctm);
-    cudaFree(ix->presence);
-    delete ix;
+    grim_free(ix);
     return code;
   };
   cudaError_t e;
-  if (layouts & GRIM_LAYOUT_TOKEN_MAJOR) {
-    e = cudaMalloc(&ix->tm, (uint64_t)v.r4 * v.wpad * sizeof(uint32_t));
-    if (e != cudaSuccess) return fail(cuda_fail(e));
-  }
-  if (layouts & GRIM_LAYOUT_BIN_MAJOR) {
-    e = cudaMalloc(&ix->bm, bm_bins * v.wpb * sizeof(uint32_t));
-    if (e != cudaSuccess) return fail(cuda_fail(e));
-  }
-  if (layouts & GRIM_LAYOUT_COARSE) {
-    e = cudaMalloc(&ix->ctm, (uint64_t)cv.r4 * cv.wpad * sizeof(uint32_t));
-    if (e != cudaSuccess) return fail(cuda_fail(e));
-  }
-  if (layouts & (GRIM_LAYOUT_COARSE | GRIM_LAYOUT_TOKEN_MAJOR)) {
-    e = cudaMalloc(&ix->presence, (uint64_t)v.r4 * sizeof(uint32_t));
-    if (e != cudaSuccess) return fail(cuda_fail(e));
-  }
-  v.tm = ix->tm;
-  v.bm = ix->bm;
-  v.presence = ix->presence;
-  ix->v = v;
-  cv.tm = ix->ctm;
-  cv.bm = nullptr;
-  cv.presence = ix->presence;
-  ix->cv = cv;
-
   // packed reference (one spare word at the end of each array for the
   // two-word reads of the token extraction)
   const uint64_t n32 = (len + 31) / 32;

@@ -54,29 +54,54 @@ struct CandArgs {
 
 constexpr int kWarps = 8;
 constexpr uint32_t kDefaultCandUnroll = 4;
+constexpr int kRegPlanes = 4;  // bit planes held in registers: multiplicities up to 15
+
+// per-warp shared memory: the multiplicity histogram, then bit planes
+// kRegPlanes..7 of the read (used only by reads with a token repeated 16+ times)
+__host__ __device__ constexpr uint32_t hist_words_of(uint32_t r4) { return r4 >= 4 ? r4 / 4 : 1; }
+__host__ __device__ constexpr uint32_t warp_smem_words(uint32_t r4, uint32_t wpb) {
+  return hist_words_of(r4) + (8 - kRegPlanes) * wpb;
+}
+
+template <int U, int CPW>
+__device__ __forceinline__ void load_ids(const int32_t* __restrict__ cand, uint64_t kb, uint64_t c1,
+                                         uint32_t slot, uint32_t (&b)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const uint64_t k = kb + (uint64_t)u * CPW + slot;
+    b[u] = k < c1 ? (uint32_t)__ldg(cand + k) : 0u;
+  }
+}
 
 template <int WPB, int U>
 __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
   using C = Cfg<WPB>;
   constexpr int WL = C::WL, G = C::G, CPW = C::CPW;
-  extern __shared__ uint32_t s_hist[];  // [warps][hist_words]: byte t = multiplicity of token t
+  extern __shared__ uint32_t s_warp[];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t r4 = a.ix.r4;
-  const uint32_t hist_words = r4 >= 4 ? r4 / 4 : 1;
-  uint32_t* hist = s_hist + warp * hist_words;
+  const uint32_t hist_words = hist_words_of(r4);
+  uint32_t* hist = s_warp + warp * warp_smem_words(r4, WPB);  // byte t = multiplicity of token t
+  uint32_t* xplanes = hist + hist_words;                        // [8 - kRegPlanes][WPB]
   const uint32_t sub = lane % G;     // this lane's slice of a bin vector
   const uint32_t slot = lane / G;    // which of the warp's CPW candidates
   if (*(volatile uint32_t*)&a.ctl->status) return;
   if (gated_off(a.ctl, a.live)) return;  // the batch takes the other path
   const uint32_t n_reads = live_reads(a.ctl, a.live, a.rv.n_reads);
 
+  // the next read is claimed one read ahead, so the atomic's latency overlaps
+  // the current read's work
+  uint32_t r_next = 0;
+  if (lane == 0) r_next = atomicAdd(&a.ctl->item, 1u);
   for (;;) {
-    uint32_t r = 0;
-    if (lane == 0) r = atomicAdd(&a.ctl->item, 1u);
-    r = __shfl_sync(0xFFFFFFFFu, r, 0);
+    const uint32_t r = __shfl_sync(0xFFFFFFFFu, r_next, 0);
     if (r >= n_reads) break;
+    if (lane == 0) r_next = atomicAdd(&a.ctl->item, 1u);
     const uint64_t c0 = a.cand_off[r], c1 = a.cand_off[r + 1];
     if (c0 == c1) continue;
+    // the first candidate ids are fetched while the histogram is built
+    uint32_t bc[U];
+    load_ids<U, CPW>(a.cand, c0, c1, slot, bc);
 
     // multiplicity histogram of the read's clean tokens (the warp has
     // finished reading the previous read's histogram)
@@ -101,50 +126,58 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
     }
     mx = __reduce_max_sync(0xFFFFFFFFu, mx);
     const uint32_t K = 32 - __clz(mx);  // planes in use
-    // bit planes k < K of the multiplicities for this lane's WL words
-    uint32_t P[8][WL];
+    // bit planes k < K of the multiplicities for this lane's WL words: the
+    // first kRegPlanes in registers, the rest (rare) in shared memory
+    uint32_t P[kRegPlanes][WL];
 #pragma unroll
     for (int w = 0; w < WL; ++w) {
       const uint32_t wi = sub * WL + w;  // word index in the vector: tokens wi*32 .. wi*32+31
-#pragma unroll
-      for (int k = 0; k < 8; ++k) P[k][w] = 0;
+      uint32_t hw[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const uint32_t h = wi * 8 + j;
-        const uint32_t hw = h < hist_words && (wi * 32 + 4 * j) < r4 ? hist[h] : 0u;
+        hw[j] = h < hist_words && (wi * 32 + 4 * j) < r4 ? hist[h] : 0u;
+      }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          if ((uint32_t)k < K) {
-            uint32_t x = (hw >> k) & 0x01010101u;  // bit k of 4 byte counters
+      for (int k = 0; k < 8; ++k) {
+        if ((uint32_t)k < K) {
+          uint32_t pk = 0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            uint32_t x = (hw[j] >> k) & 0x01010101u;  // bit k of 4 byte counters
             x |= x >> 7;
             x |= x >> 14;
-            P[k][w] |= (x & 0xFu) << (4 * j);
+            pk |= (x & 0xFu) << (4 * j);
           }
+          if (k < kRegPlanes) P[k < kRegPlanes ? k : 0][w] = pk;
+          else xplanes[(k - kRegPlanes) * WPB + wi] = pk;
+        } else if (k < kRegPlanes) {
+          P[k < kRegPlanes ? k : 0][w] = 0;
         }
       }
     }
+    if (K > kRegPlanes) __syncwarp();
     const uint32_t thr = ntok - dmax;   // pass iff sum >= (L-q+1) - min(q*e, L-q+1)
 
-    // U independent gathers in flight per lane group: load all, then count
+    // U independent gathers in flight per lane group; the ids of the next
+    // step are fetched before this step's vectors are used
     for (uint64_t kb = c0; kb < c1; kb += (uint64_t)CPW * U) {
-      uint64_t k[U];
-      uint32_t b[U], v[U][WL];
+      uint32_t bn[U];
+      load_ids<U, CPW>(a.cand, kb + (uint64_t)CPW * U, c1, slot, bn);
+      uint32_t v[U][WL];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        k[u] = kb + (uint64_t)u * CPW + slot;
-        b[u] = k[u] < c1 ? (uint32_t)__ldg(a.cand + k[u]) : 0u;
+        if (kb + (uint64_t)u * CPW + slot < c1)
+          load_words<WL>(a.ix.bm + (uint64_t)bc[u] * WPB + sub * WL, v[u]);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (k[u] < c1) load_words<WL>(a.ix.bm + (uint64_t)b[u] * WPB + sub * WL, v[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const bool valid = k[u] < c1;
+        const uint64_t k = kb + (uint64_t)u * CPW + slot;
+        const bool valid = k < c1;
         uint32_t sum = 0;
         if (valid) {
 #pragma unroll
-          for (int p = 0; p < 8; ++p) {
+          for (int p = 0; p < kRegPlanes; ++p) {
             if ((uint32_t)p < K) {
               uint32_t s = 0;
 #pragma unroll
@@ -152,12 +185,19 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
               sum += s << p;
             }
           }
+          for (uint32_t p = kRegPlanes; p < K; ++p) {
+            uint32_t s = 0;
+#pragma unroll
+            for (int w = 0; w < WL; ++w)
+              s += __popc(v[u][w] & xplanes[(p - kRegPlanes) * WPB + sub * WL + w]);
+            sum += s << p;
+          }
         }
 #pragma unroll
         for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
         // bins past num_bins exist only as zero padding of the table (members
         // of the last super-bin); they never pass
-        const bool real = valid && b[u] < a.ix.num_bins;
+        const bool real = valid && bc[u] < a.ix.num_bins;
         const bool pass = real && sub == 0 && sum >= thr;
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
         if (bal) {
@@ -167,20 +207,21 @@ __global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
           if (pass) {
             const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
             if (pos < a.rec.cap) {
-              a.rec.keys[pos] = k[u];
+              a.rec.keys[pos] = k;
               a.rec.counts[pos] = (uint8_t)sum;
             }
           }
         }
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) bc[u] = bn[u];
     }
   }
 }
 
 template <int WPB, int U>
 void launch_u(const CandArgs& a, cudaStream_t st, const char* name) {
-  const uint32_t hist_words = a.ix.r4 >= 4 ? a.ix.r4 / 4 : 1;
-  const size_t smem = (size_t)kWarps * hist_words * sizeof(uint32_t);
+  const size_t smem = (size_t)kWarps * warp_smem_words(a.ix.r4, WPB) * sizeof(uint32_t);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

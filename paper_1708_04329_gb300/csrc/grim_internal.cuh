@@ -32,9 +32,10 @@ struct Ctl {
   uint32_t live_reads;             // reads in this batch
   uint32_t path;                   // kPathCoarse / kPathExact
   unsigned long long live_cand;    // candidates in this batch
+  unsigned long long live_bases;   // read bytes in this batch (host-memory plans)
   unsigned long long n_surv;       // survivors of the coarse pass
   unsigned long long n_final;      // passing records of the batch
-  uint32_t pad[48];
+  uint32_t pad[46];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte slot");
 static_assert(offsetof(Ctl, live_reads) == 32, "live counts follow the per-pass counters");
@@ -111,10 +112,12 @@ void launch_row_popcount(const uint32_t* tm, uint32_t rows, uint64_t words_per_r
 
 // max_e: reads with a larger budget are an argument error (graph launches
 // fix the counter depth from it); 0xFFFF = no limit
+// max_bases: size of the reads buffer when known (a read ending past it
+// fails the batch with kStatusArg), else ~0
 void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t* lens,
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
                      uint32_t* meta, Ctl* ctl, cudaStream_t st, Live live = {false, 0},
-                     uint32_t max_e = 0xFFFFu);
+                     uint32_t max_e = 0xFFFFu, uint64_t max_bases = ~0ull);
 void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
                              uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st,
                              Live live = {false, 0});
@@ -242,6 +245,13 @@ struct grim_index {
 };
 
 namespace grim {
+// Validate an index's parameters and allocate its (unwritten) tables; the
+// views of the returned index point at them.  GRIM_* status.
+int index_alloc(uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len, uint32_t layouts,
+                uint32_t f, grim_index** out);
+// Keep the CUDA error string for grim_last_cuda_error; the matching status.
+int record_cuda_error(cudaError_t e);
+
 // the all-bins filter can run coarse-then-exact when the index has both the
 // coarse table and the bin-major table
 inline bool two_level_capable(const grim_index* idx) {

@@ -21,14 +21,48 @@
 namespace grim {
 namespace {
 
-// the first 16 bytes of Ctl::live_reads.. written by each launch
+// the 24 bytes of Ctl::live_reads..live_bases written by each launch
 struct BatchHeader {
   uint32_t n_reads;
   uint32_t path;  // written 0: the control kernel decides
   unsigned long long n_cand;
+  unsigned long long n_bases;
 };
-static_assert(sizeof(BatchHeader) == 16, "header mirrors Ctl::live_reads..live_cand");
+static_assert(sizeof(BatchHeader) == 24, "header mirrors Ctl::live_reads..live_bases");
 static_assert(offsetof(Ctl, live_cand) - offsetof(Ctl, live_reads) == 8, "header layout");
+static_assert(offsetof(Ctl, live_bases) - offsetof(Ctl, live_reads) == 16, "header layout");
+
+// Host-memory plans: the batch's inputs are read from mapped pinned host
+// memory into the device buffers by the graph itself, as many bytes as the
+// batch's counts say.  Segment sizes are rounded up to 16 bytes inside
+// 256-byte-aligned slots on both sides.
+enum : uint32_t { kCountBases = 0, kCountReads = 1, kCountCand = 2, kCountReads1 = 3 };
+struct CopySeg {
+  const uint4* src;
+  uint4* dst;
+  uint32_t unit;      // bytes per counted element
+  uint32_t count_of;  // kCount*
+  uint64_t cap;       // bytes the slot holds
+};
+constexpr int kCopySegs = 6;
+struct CopyIn {
+  CopySeg s[kCopySegs];
+};
+
+__global__ void k_copy_in(CopyIn a, const Ctl* c) {
+  const CopySeg& g = a.s[blockIdx.y];
+  if (!g.src) return;
+  const uint64_t n = g.count_of == kCountBases  ? c->live_bases
+                     : g.count_of == kCountCand ? c->live_cand
+                     : g.count_of == kCountReads ? (uint64_t)c->live_reads
+                                                 : (uint64_t)c->live_reads + 1;
+  uint64_t bytes = n * g.unit;
+  if (bytes > g.cap) bytes = g.cap;
+  const uint64_t n16 = (bytes + 15) / 16;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n16;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    g.dst[i] = g.src[i];
+}
 
 enum : uint32_t { kCtlDecide = 1, kCtlAfterCoarse = 2, kCtlFinal = 3 };
 
@@ -65,7 +99,12 @@ struct grim_plan {
   uint32_t f;            // coarse factor (0: no coarse path)
   Layout L;
   char* dev;             // one allocation: inputs, outputs, workspace
-  grim_plan_buffers buf;
+  grim_plan_buffers buf;   // what the caller fills and reads
+  grim_plan_buffers dbuf;  // what the graph reads and writes
+  bool hio;                // GRIM_PLAN_HOST_IO
+  char* hin;             // mapped pinned inputs (host-memory plans)
+  char* hout;            // mapped pinned outputs (host-memory plans)
+  CopyIn copy;
   Ctl* ctl;
   BatchHeader* header;   // pinned
   Ctl* result;           // pinned
@@ -107,20 +146,22 @@ int capture(grim_plan* p) {
     prof_suspend(false);
     return GRIM_E_CUDA;
   }
+  const grim_plan_buffers& B = p->dbuf;
   cudaMemsetAsync(p->ctl, 0, sizeof(Ctl), st);
   cudaMemcpyAsync(&p->ctl->live_reads, p->header, sizeof(BatchHeader), cudaMemcpyHostToDevice, st);
-  launch_tokenise(p->buf.reads, p->buf.offsets, p->buf.lens, p->buf.e, v, rv,
+  if (p->hio) k_copy_in<<<dim3(64, kCopySegs), 256, 0, st>>>(p->copy, p->ctl);
+  launch_tokenise(B.reads, B.offsets, B.lens, B.e, v, rv,
                   reinterpret_cast<uint16_t*>(ws + L.tok), reinterpret_cast<uint32_t*>(ws + L.meta),
-                  p->ctl, st, live, d.max_e);
+                  p->ctl, st, live, d.max_e, d.max_bases);
   if (p->cand_mode) {
-    launch_check_candidates(p->buf.cand, p->buf.cand_off, d.max_reads, d.max_cand, v.num_bins,
+    launch_check_candidates(B.cand, B.cand_off, d.max_reads, d.max_cand, v.num_bins,
                             p->ctl, st, live);
-    launch_candidates(v, rv, p->buf.cand, p->buf.cand_off, ra, p->ctl, st, "candidates", live,
+    launch_candidates(v, rv, B.cand, B.cand_off, ra, p->ctl, st, "candidates", live,
                       d.cand_unroll);
     k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlFinal, 0, 0, 0);
     sort_and_emit(ra, rb, d.cap, bit_length(d.max_cand ? d.max_cand - 1 : 0), ws + L.hist, true,
-                  bin_bits, p->buf.cand, p->buf.cand_off, d.max_reads, p->buf.out_read,
-                  p->buf.out_bin, p->buf.out_count, st, &p->ctl->n_final, &p->ctl->live_reads);
+                  bin_bits, B.cand, B.cand_off, d.max_reads, B.out_read,
+                  B.out_bin, B.out_count, st, &p->ctl->n_final, &p->ctl->live_reads);
   } else {
     k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlDecide, p->f != 0, has_exact, rcap);
     int32_t* icand = reinterpret_cast<int32_t*>(ws + L.cand);
@@ -145,12 +186,12 @@ int capture(grim_plan* p) {
     k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlFinal, 0, 0, 0);
     if (p->f) {
       sort_and_emit(ra, rb, d.cap, bit_length(rcap * p->f - 1), ws + L.hist, true, bin_bits, icand,
-                    ioff, d.max_reads, p->buf.out_read, p->buf.out_bin, p->buf.out_count, st,
+                    ioff, d.max_reads, B.out_read, B.out_bin, B.out_count, st,
                     &p->ctl->n_final, &p->ctl->live_reads, p->ctl, kPathCoarse);
     }
     if (has_exact) {
       sort_and_emit(ra, rb, d.cap, bin_bits + read_bits, ws + L.hist, false, bin_bits, nullptr,
-                    nullptr, d.max_reads, p->buf.out_read, p->buf.out_bin, p->buf.out_count, st,
+                    nullptr, d.max_reads, B.out_read, B.out_bin, B.out_count, st,
                     &p->ctl->n_final, &p->ctl->live_reads, p->ctl, kPathExact);
     }
   }
@@ -169,6 +210,8 @@ void destroy(grim_plan* p) {
   if (p->done) cudaEventDestroy(p->done);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   cudaFree(p->dev);
+  if (p->hin) cudaFreeHost(p->hin);
+  if (p->hout) cudaFreeHost(p->hout);
   cudaFreeHost(p->header);
   cudaFreeHost(p->result);
   delete p;
@@ -184,7 +227,9 @@ int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_pla
   if (!idx || !desc || desc->max_reads == 0 || desc->max_bases == 0) return GRIM_E_ARG;
   if (desc->cap > 0xFFFFFFFFull || desc->max_e > 0xFFFFu || desc->cand_unroll > 8)
     return GRIM_E_ARG;
+  if (desc->flags & ~(GRIM_PLAN_CANDIDATES | GRIM_PLAN_HOST_IO)) return GRIM_E_ARG;
   const bool cand_mode = (desc->flags & GRIM_PLAN_CANDIDATES) != 0;
+  const bool hio = (desc->flags & GRIM_PLAN_HOST_IO) != 0;
   if (cand_mode && !(idx->layouts & GRIM_LAYOUT_BIN_MAJOR)) return GRIM_E_NO_LAYOUT;
   if (!cand_mode && !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR) && !two_level_capable(idx))
     return GRIM_E_NO_LAYOUT;
@@ -193,6 +238,7 @@ int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_pla
   p->idx = idx;
   p->d = *desc;
   p->cand_mode = cand_mode;
+  p->hio = hio;
   p->f = (!cand_mode && two_level_capable(idx)) ? idx->factor : 0;
   p->L = layout(idx->v, desc->max_reads, desc->cap, p->f);
   const uint64_t n = desc->max_reads;
@@ -204,12 +250,18 @@ int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_pla
   const uint64_t o_e = align256(o_lens + n * 4);
   const uint64_t o_cand = align256(o_e + n * 2);
   const uint64_t o_coff = align256(o_cand + mc * 4);
-  const uint64_t o_or = align256(o_coff + (cand_mode ? (n + 1) * 8 : 0));
+  const uint64_t o_in_end = align256(o_coff + (cand_mode ? (n + 1) * 8 : 0));
+  // outputs: device buffers, or mapped host memory the final kernel writes
+  const uint64_t o_or = 0;
   const uint64_t o_ob = align256(o_or + desc->cap * 4);
   const uint64_t o_oc = align256(o_ob + desc->cap * 4);
-  const uint64_t o_ws = align256(o_oc + desc->cap);
+  const uint64_t out_bytes = align256(o_oc + desc->cap);
+  const uint64_t o_out = o_in_end;
+  const uint64_t o_ws = hio ? o_in_end : o_out + out_bytes;
   const uint64_t total = o_ws + p->L.total;
   cudaError_t e = cudaMalloc(&p->dev, total);
+  if (e == cudaSuccess && hio) e = cudaHostAlloc(&p->hin, o_in_end, cudaHostAllocMapped);
+  if (e == cudaSuccess && hio) e = cudaHostAlloc(&p->hout, out_bytes, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaMallocHost(&p->header, sizeof(BatchHeader));
   if (e == cudaSuccess) e = cudaMallocHost(&p->result, sizeof(Ctl));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
@@ -218,20 +270,59 @@ int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_pla
     destroy(p);
     return e == cudaErrorMemoryAllocation ? GRIM_E_NOMEM : GRIM_E_CUDA;
   }
-  char* b = p->dev;
-  p->buf.reads = b + o_reads;
-  p->buf.offsets = reinterpret_cast<uint64_t*>(b + o_off);
-  p->buf.lens = reinterpret_cast<uint32_t*>(b + o_lens);
-  p->buf.e = reinterpret_cast<uint16_t*>(b + o_e);
-  p->buf.cand = cand_mode ? reinterpret_cast<int32_t*>(b + o_cand) : nullptr;
-  p->buf.cand_off = cand_mode ? reinterpret_cast<uint64_t*>(b + o_coff) : nullptr;
-  p->buf.out_read = reinterpret_cast<uint32_t*>(b + o_or);
-  p->buf.out_bin = reinterpret_cast<uint32_t*>(b + o_ob);
-  p->buf.out_count = reinterpret_cast<uint8_t*>(b + o_oc);
-  p->ctl = reinterpret_cast<Ctl*>(b + o_ws);
+  auto inputs = [&](char* b, grim_plan_buffers& f) {
+    f.reads = b + o_reads;
+    f.offsets = reinterpret_cast<uint64_t*>(b + o_off);
+    f.lens = reinterpret_cast<uint32_t*>(b + o_lens);
+    f.e = reinterpret_cast<uint16_t*>(b + o_e);
+    f.cand = cand_mode ? reinterpret_cast<int32_t*>(b + o_cand) : nullptr;
+    f.cand_off = cand_mode ? reinterpret_cast<uint64_t*>(b + o_coff) : nullptr;
+  };
+  auto outputs = [&](char* b, grim_plan_buffers& f) {
+    f.out_read = reinterpret_cast<uint32_t*>(b + o_or);
+    f.out_bin = reinterpret_cast<uint32_t*>(b + o_ob);
+    f.out_count = reinterpret_cast<uint8_t*>(b + o_oc);
+  };
+  inputs(p->dev, p->dbuf);
+  if (hio) {
+    void* hout_dev = nullptr;
+    e = cudaHostGetDevicePointer(&hout_dev, p->hout, 0);
+    if (e != cudaSuccess) {
+      destroy(p);
+      return GRIM_E_CUDA;
+    }
+    outputs(static_cast<char*>(hout_dev), p->dbuf);
+    inputs(p->hin, p->buf);
+    outputs(p->hout, p->buf);
+    void* hin_dev = nullptr;
+    e = cudaHostGetDevicePointer(&hin_dev, p->hin, 0);
+    if (e != cudaSuccess) {
+      destroy(p);
+      return GRIM_E_CUDA;
+    }
+    const uint64_t in_off[kCopySegs] = {o_reads, o_off, o_lens, o_e, o_cand, o_coff};
+    const uint64_t in_end[kCopySegs] = {o_off, o_lens, o_e, o_cand, o_coff, o_in_end};
+    const uint32_t unit[kCopySegs] = {1, 8, 4, 2, 4, 8};
+    const uint32_t cnt[kCopySegs] = {kCountBases, kCountReads, kCountReads, kCountReads,
+                                     kCountCand, kCountReads1};
+    for (int i = 0; i < kCopySegs; ++i) {
+      const bool used = i < 4 || cand_mode;
+      p->copy.s[i].src = used ? reinterpret_cast<const uint4*>(static_cast<char*>(hin_dev) + in_off[i])
+                              : nullptr;
+      p->copy.s[i].dst = reinterpret_cast<uint4*>(p->dev + in_off[i]);
+      p->copy.s[i].unit = unit[i];
+      p->copy.s[i].count_of = cnt[i];
+      p->copy.s[i].cap = in_end[i] - in_off[i];
+    }
+  } else {
+    outputs(p->dev + o_out, p->dbuf);
+    p->buf = p->dbuf;
+  }
+  p->ctl = reinterpret_cast<Ctl*>(p->dev + o_ws);
   p->header->n_reads = 0;
   p->header->path = 0;
   p->header->n_cand = 0;
+  p->header->n_bases = 0;
   const int rc = capture(p);
   if (rc != GRIM_OK) {
     destroy(p);
@@ -253,9 +344,19 @@ int grim_plan_launch(grim_plan* p, uint32_t n_reads, uint64_t n_cand, void* stre
   // the header is read by the graph's first node: wait until the previous
   // run of this plan has consumed it
   if (p->launched && cudaEventSynchronize(p->done) != cudaSuccess) return GRIM_E_CUDA;
+  uint64_t n_bases = 0;
+  if (p->hio) {
+    // the graph copies the reads' bytes [0, n_bases): every read must lie inside
+    for (uint32_t i = 0; i < n_reads; ++i) {
+      const uint64_t o = p->buf.offsets[i], l = p->buf.lens[i];
+      if (o > p->d.max_bases || l > p->d.max_bases - o) return GRIM_E_ARG;
+      if (o + l > n_bases) n_bases = o + l;
+    }
+  }
   p->header->n_reads = n_reads;
   p->header->path = 0;
   p->header->n_cand = p->cand_mode ? n_cand : 0;
+  p->header->n_bases = n_bases;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e = cudaGraphLaunch(p->exec, st);
   if (e == cudaSuccess) e = cudaEventRecord(p->done, st);

@@ -24,7 +24,7 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
     const uint32_t* __restrict__ lens, const uint16_t* __restrict__ e, uint32_t n_reads, uint32_t q,
     uint32_t max_read_len, uint32_t r4, uint32_t ts, const uint32_t* __restrict__ presence,
     uint16_t* __restrict__ tokens, uint32_t* __restrict__ meta, Ctl* ctl, Live live,
-    uint32_t max_e) {
+    uint32_t max_e, uint64_t max_bases) {
   __shared__ unsigned long long s_key[kTokWarps][kMaxStride];
   __shared__ uint16_t s_row[kTokWarps][kMaxStride];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -40,6 +40,9 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
     bad = true;
   } else if (L > max_read_len || L - q + 1 > kMaxTokens) {
     if (lane == 0) atomicOr(&ctl->status, kStatusLong);
+    bad = true;
+  } else if (off > max_bases || L > max_bases - off) {  // past the end of the reads buffer
+    if (lane == 0) atomicOr(&ctl->status, kStatusArg);
     bad = true;
   }
   const uint32_t ntok = bad ? 0 : L - q + 1;
@@ -105,14 +108,15 @@ __global__ void k_check_candidates(const int32_t* __restrict__ cand,
 
 void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t* lens,
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
-                     uint32_t* meta, Ctl* ctl, cudaStream_t st, Live live, uint32_t max_e) {
+                     uint32_t* meta, Ctl* ctl, cudaStream_t st, Live live, uint32_t max_e,
+                     uint64_t max_bases) {
   if (rv.n_reads == 0) return;
   const uint32_t threads = kTokWarps * 32;
   uint64_t grid = ((uint64_t)rv.n_reads * 32 + threads - 1) / threads;
   ProfScope ps("tokenise", st);
   k_tokenise<<<(unsigned)grid, threads, 0, st>>>(reads, offsets, lens, e, rv.n_reads, ix.q,
                                                  ix.max_read_len, ix.r4, rv.ts, ix.presence, tokens,
-                                                 meta, ctl, live, max_e);
+                                                 meta, ctl, live, max_e, max_bases);
 }
 
 void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,

@@ -28,7 +28,12 @@ GRIM_E_WORKSPACE = -9
 GRIM_E_NO_LAYOUT = -10
 GRIM_E_UNSUPPORTED = -11
 GRIM_E_NOT_READY = -12
+GRIM_E_BUSY = -13
+GRIM_E_IO = -14
+GRIM_E_FORMAT = -15
+GRIM_LOAD_VERIFY = 1
 GRIM_PLAN_CANDIDATES = 1
+GRIM_PLAN_HOST_IO = 2
 
 GRIM_LAYOUT_TOKEN_MAJOR = 1
 GRIM_LAYOUT_BIN_MAJOR = 2
@@ -44,6 +49,8 @@ EXPORTS = (
     "grim_filter_noalloc", "grim_last_filter_stats", "grim_build_ex", "grim_build_host_ex",
     "grim_plan_create", "grim_plan_buffers_get", "grim_plan_launch", "grim_plan_query",
     "grim_plan_wait", "grim_plan_device_bytes", "grim_plan_free", "grim_default_coarse_factor",
+    "grim_server_create", "grim_server_submit", "grim_server_wait", "grim_server_take",
+    "grim_server_stats_get", "grim_server_free", "grim_save", "grim_load",
 )
 
 
@@ -86,6 +93,27 @@ class _PlanDesc(C.Structure):
 class _PlanBuffers(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("reads", "offsets", "lens", "e", "cand", "cand_off",
                                            "out_read", "out_bin", "out_count")]
+
+
+class _ServerDesc(C.Structure):
+    _fields_ = [("slots", C.c_uint32), ("max_reads", C.c_uint32), ("max_bases", C.c_uint64),
+                ("max_cand", C.c_uint64), ("cap", C.c_uint64), ("max_e", C.c_uint32),
+                ("flags", C.c_uint32), ("mem_budget", C.c_uint64),
+                ("max_queued_reads", C.c_uint64), ("cand_unroll", C.c_uint32),
+                ("reserved", C.c_uint32 * 7)]
+
+
+class _RequestInfo(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_reads", C.c_uint32), ("n_out", C.c_uint64),
+                ("batch", C.c_uint64), ("batch_requests", C.c_uint32),
+                ("batch_reads", C.c_uint32), ("t_submit_ns", C.c_uint64),
+                ("t_launch_ns", C.c_uint64), ("t_done_ns", C.c_uint64)]
+
+
+class _ServerStats(C.Structure):
+    _fields_ = [("slots", C.c_uint32), ("reserved", C.c_uint32), ("device_bytes", C.c_uint64)] + [
+        (n, C.c_uint64) for n in ("submitted", "completed", "batches", "batch_reads", "reads_done",
+                                  "records", "overflow_splits", "queued_requests", "queued_reads")]
 
 
 class _KTime(C.Structure):
@@ -152,6 +180,22 @@ def _lib() -> C.CDLL:
         lib.grim_plan_free.restype = None
         lib.grim_plan_free.argtypes = [vp]
         lib.grim_profile.restype = i32
+        lib.grim_save.restype = i32
+        lib.grim_save.argtypes = [vp, C.c_char_p]
+        lib.grim_load.restype = i32
+        lib.grim_load.argtypes = [C.c_char_p, u32, u32, pp]
+        lib.grim_server_create.restype = i32
+        lib.grim_server_create.argtypes = [vp, C.POINTER(_ServerDesc), pp]
+        lib.grim_server_submit.restype = i32
+        lib.grim_server_submit.argtypes = [vp, vp, vp, vp, u32, vp, vp, vp, C.POINTER(C.c_uint64)]
+        lib.grim_server_wait.restype = i32
+        lib.grim_server_wait.argtypes = [vp, u64, C.c_int64]
+        lib.grim_server_take.restype = i32
+        lib.grim_server_take.argtypes = [vp, u64, vp, vp, vp, u64, C.POINTER(_RequestInfo)]
+        lib.grim_server_stats_get.restype = i32
+        lib.grim_server_stats_get.argtypes = [vp, C.POINTER(_ServerStats)]
+        lib.grim_server_free.restype = None
+        lib.grim_server_free.argtypes = [vp]
         lib.grim_profile.argtypes = [i32]
         lib.grim_profile_get.restype = i32
         lib.grim_profile_get.argtypes = [C.POINTER(_KTime), i32]
@@ -350,6 +394,23 @@ def grim_build_host_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GR
                                    _stream_ptr(stream), C.byref(h))
     if rc != GRIM_OK:
         raise GrimError(rc, "grim_build_host_ex")
+    return GrimIndex(h.value)
+
+
+def grim_save(index: GrimIndex, path) -> None:
+    """Write the index (parameters and every table it holds) to a file."""
+    rc = _lib().grim_save(index.handle, str(path).encode())
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_save")
+
+
+def grim_load(path, layouts: int = 0, verify: bool = False) -> GrimIndex:
+    """Read an index written by grim_save (``layouts``: tables to load, 0 = all)."""
+    h = C.c_void_p()
+    rc = _lib().grim_load(str(path).encode(), layouts, GRIM_LOAD_VERIFY if verify else 0,
+                          C.byref(h))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_load")
     return GrimIndex(h.value)
 
 
@@ -565,6 +626,7 @@ class GrimPlan:
         self.max_cand = int(desc.max_cand)
         self.cap = int(desc.cap)
         self.candidates = bool(desc.flags & GRIM_PLAN_CANDIDATES)
+        self.host_io = bool(desc.flags & GRIM_PLAN_HOST_IO)
         self.buffers = grim_plan_buffers_get(self)
 
     @property
@@ -585,13 +647,25 @@ class GrimPlan:
             pass
 
     def stage(self, reads, offsets, lens, e, cand=None, cand_off=None):
-        """Copy one batch (CUDA or pinned CPU tensors) into the plan's buffers
-        on the current stream."""
+        """Copy one batch into the plan's buffers: CUDA or pinned CPU tensors
+        on the current stream, or host arrays for a host-memory plan."""
         b = self.buffers
-        n = int(lens.numel())
-        nb = int(reads.numel())
+        n = len(lens)
+        nb = len(reads)
         if n > self.max_reads or nb > self.max_bases:
             raise ValueError("batch larger than the plan")
+        if self.host_io:
+            for name, x in (("reads", reads), ("offsets", offsets), ("lens", lens), ("e", e)):
+                a = np.asarray(x.cpu() if hasattr(x, "cpu") else x).reshape(-1)
+                b[name][:len(a)] = a.view(b[name].dtype)
+            if self.candidates:
+                c = np.asarray(cand).reshape(-1)
+                if len(c) > self.max_cand:
+                    raise ValueError("more candidates than the plan holds")
+                b["cand"][:len(c)] = c.view(np.int32)
+                b["cand_off"][:n + 1] = np.asarray(cand_off).reshape(-1).view(np.uint64)
+                return n, len(c)
+            return n, 0
         b["reads"][:nb].copy_(reads.view(b["reads"].dtype), non_blocking=True)
         b["offsets"][:n].copy_(offsets.view(b["offsets"].dtype), non_blocking=True)
         b["lens"][:n].copy_(lens.view(b["lens"].dtype), non_blocking=True)
@@ -612,13 +686,16 @@ class GrimPlan:
         grim_plan_launch(self, n, nc, stream)
         k = grim_plan_wait(self)
         b = self.buffers
-        return b["out_read"][:k], b["out_bin"][:k], b["out_count"][:k]
+        out = b["out_read"][:k], b["out_bin"][:k], b["out_count"][:k]
+        return tuple(x.copy() for x in out) if self.host_io else out
 
 
 def grim_plan_create(index: GrimIndex, max_reads: int, max_bases: int, max_e: int, cap: int,
-                     max_cand: int = 0, candidates: bool = False, cand_unroll: int = 0) -> GrimPlan:
+                     max_cand: int = 0, candidates: bool = False, cand_unroll: int = 0,
+                     host_io: bool = False) -> GrimPlan:
     d = _PlanDesc(max_reads, max_e, max_bases, max_cand, cap,
-                  GRIM_PLAN_CANDIDATES if candidates else 0, cand_unroll)
+                  (GRIM_PLAN_CANDIDATES if candidates else 0) | (GRIM_PLAN_HOST_IO if host_io else 0),
+                  cand_unroll)
     h = C.c_void_p()
     rc = _lib().grim_plan_create(index.handle, C.byref(d), C.byref(h))
     if rc != GRIM_OK:
@@ -626,8 +703,15 @@ def grim_plan_create(index: GrimIndex, max_reads: int, max_bases: int, max_e: in
     return GrimPlan(h.value, index, d)
 
 
+#: element types of a host-memory plan's buffers (the C types of grim.h)
+_HOST_TYPES = {"reads": np.uint8, "offsets": np.uint64, "lens": np.uint32, "e": np.uint16,
+               "cand": np.int32, "cand_off": np.uint64, "out_read": np.uint32,
+               "out_bin": np.uint32, "out_count": np.uint8}
+
+
 def grim_plan_buffers_get(plan: GrimPlan) -> dict:
-    """The plan's device buffers as zero-copy CUDA tensors."""
+    """The plan's buffers as zero-copy CUDA tensors (numpy arrays over the
+    mapped host memory of a host-memory plan)."""
     torch = _torch()
     b = _PlanBuffers()
     rc = _lib().grim_plan_buffers_get(plan.handle, C.byref(b))
@@ -642,7 +726,12 @@ def grim_plan_buffers_get(plan: GrimPlan) -> dict:
     for name, (n, ts) in spec.items():
         ptr = getattr(b, name)
         if ptr and n:
-            out[name] = torch.as_tensor(_CudaArray(ptr, (n,), ts, plan), device="cuda")
+            if plan.host_io:
+                dt = np.dtype(_HOST_TYPES[name])
+                raw = (C.c_char * (n * dt.itemsize)).from_address(ptr)
+                out[name] = np.frombuffer(raw, dtype=dt)
+            else:
+                out[name] = torch.as_tensor(_CudaArray(ptr, (n,), ts, plan), device="cuda")
     return out
 
 
@@ -679,3 +768,150 @@ def grim_plan_device_bytes(plan: GrimPlan) -> int:
 
 def grim_plan_free(plan: GrimPlan) -> None:
     plan.close()
+
+
+# ---------------------------------------------------------------------------
+# serving: continuous batching over a resident index
+# ---------------------------------------------------------------------------
+
+@dataclass
+class RequestInfo:
+    status: int
+    n_reads: int
+    n_out: int
+    batch: int
+    batch_requests: int
+    batch_reads: int
+    t_submit_ns: int
+    t_launch_ns: int
+    t_done_ns: int
+
+    @property
+    def latency_s(self) -> float:
+        return (self.t_done_ns - self.t_submit_ns) * 1e-9
+
+
+class GrimServer:
+    """Owns a grim_server handle (and keeps its index alive)."""
+
+    def __init__(self, handle: int, index: GrimIndex, desc: _ServerDesc):
+        self._h = handle
+        self.index = index
+        self.candidates = bool(desc.flags & GRIM_PLAN_CANDIDATES)
+        self.cap = int(desc.cap)
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("server already freed")
+        return self._h
+
+    def close(self) -> None:
+        if self._h:
+            _lib().grim_server_free(self._h)
+            self._h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, reads, offsets, lens, e, cand=None, cand_off=None) -> int:
+        return grim_server_submit(self, reads, offsets, lens, e, cand, cand_off)
+
+    def result(self, ticket: int, timeout_s: float | None = None):
+        """Wait for a request and take its pass list: ((read, bin, count), RequestInfo)."""
+        grim_server_wait(self, ticket, timeout_s)
+        return grim_server_take(self, ticket)
+
+    def stats(self) -> dict:
+        return grim_server_stats_get(self)
+
+
+def grim_server_create(index: GrimIndex, slots: int, max_reads: int, max_bases: int, max_e: int,
+                       cap: int, max_cand: int = 0, candidates: bool = False,
+                       mem_budget: int = 0, max_queued_reads: int = 0,
+                       cand_unroll: int = 0) -> GrimServer:
+    d = _ServerDesc(slots, max_reads, max_bases, max_cand, cap, max_e,
+                    GRIM_PLAN_CANDIDATES if candidates else 0, mem_budget, max_queued_reads,
+                    cand_unroll)
+    h = C.c_void_p()
+    rc = _lib().grim_server_create(index.handle, C.byref(d), C.byref(h))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_server_create")
+    return GrimServer(h.value, index, d)
+
+
+def grim_server_submit(server: GrimServer, reads, offsets, lens, e, cand=None,
+                       cand_off=None) -> int:
+    """Queue one request (host arrays, copied before return); returns its ticket."""
+    pr, kr = _hptr(reads, "reads", np.uint8)
+    po, ko = _hptr(offsets, "offsets", np.uint64)
+    pl, kl = _hptr(lens, "lens", np.uint32)
+    pe, ke = _hptr(e, "e", np.uint16)
+    pc, kc = _hptr(cand, "cand", np.int32)
+    pco, kco = _hptr(cand_off, "cand_off", np.uint64)
+    t = C.c_uint64(0)
+    rc = _lib().grim_server_submit(server.handle, pr, po, pl, len(lens), pe, pc or None,
+                                   pco or None, C.byref(t))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_server_submit")
+    return int(t.value)
+
+
+def grim_server_wait(server: GrimServer, ticket: int, timeout_s: float | None = None) -> bool:
+    """True once the request has completed; False on timeout."""
+    us = -1 if timeout_s is None else int(timeout_s * 1e6)
+    rc = _lib().grim_server_wait(server.handle, ticket, us)
+    if rc == GRIM_E_NOT_READY:
+        return False
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_server_wait")
+    return True
+
+
+def grim_server_take(server: GrimServer, ticket: int):
+    """Take a completed request's pass list: ((read, bin, count), RequestInfo)."""
+    info = _RequestInfo()
+    cap = 0
+    o_r = o_b = o_c = None
+    while True:
+        rc = _lib().grim_server_take(
+            server.handle, ticket, o_r.ctypes.data if o_r is not None else None,
+            o_b.ctypes.data if o_b is not None else None,
+            o_c.ctypes.data if o_c is not None else None, cap, C.byref(info))
+        if rc != GRIM_E_OVERFLOW or info.status != GRIM_OK:
+            break
+        cap = int(info.n_out)  # the request is kept: take it again with room for it
+        o_r = np.empty(cap, np.uint32)
+        o_b = np.empty(cap, np.uint32)
+        o_c = np.empty(cap, np.uint8)
+    ri = RequestInfo(*(getattr(info, f) for f, _ in _RequestInfo._fields_))
+    if rc != GRIM_OK:
+        err = GrimError(rc, "grim_server_take")
+        err.n_out = int(info.n_out)
+        err.info = ri
+        raise err
+    n = int(info.n_out)
+    if o_r is None:
+        o_r, o_b, o_c = np.empty(0, np.uint32), np.empty(0, np.uint32), np.empty(0, np.uint8)
+    return (o_r[:n], o_b[:n], o_c[:n]), ri
+
+
+def grim_server_stats_get(server: GrimServer) -> dict:
+    st = _ServerStats()
+    rc = _lib().grim_server_stats_get(server.handle, C.byref(st))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_server_stats_get")
+    return {f: int(getattr(st, f)) for f, _ in _ServerStats._fields_ if f != "reserved"}
+
+
+def grim_server_free(server: GrimServer) -> None:
+    server.close()

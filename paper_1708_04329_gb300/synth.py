@@ -212,3 +212,30 @@ def finer_index(n_reads: int = 1_000_000, n: int = HUMAN_N, g: np.ndarray | None
     off, cand = candidates((rs.true_pos // 100).astype(np.int32), num_bins, seed=5)
     return dict(name="finer_index", genome=g, B=100, q=6, max_read_len=150, reads=rs,
                 cand_off=off, cand=cand)
+
+
+def serving(pool_reads: int = 2_000_000, n: int = HUMAN_N, g: np.ndarray | None = None) -> dict:
+    """Serving workload: the human-scale genome (B=200, q=5, index built with
+    max_read_len=250) and a pool of reads with L in {100,150,250} w.p.
+    .5/.3/.2 and e_r uniform in {0..floor(0.05 L)} (seed 6), from which the
+    requests of a trace are cut."""
+    g = human_genome(n) if g is None else g
+    rs = reads(g, pool_reads, seed=6, lengths=(100, 150, 250), probs=(0.5, 0.3, 0.2),
+               e_frac=(5, 100), max_edits=None)
+    return dict(name="serving", genome=g, B=200, q=5, max_read_len=250, reads=rs)
+
+
+def request_trace(duration_s: float, rate: float, pool: int, seed: int = 6,
+                  max_batch: int = 8192) -> dict:
+    """Poisson arrivals of read batches: exponential gaps of mean 1/rate
+    seconds over ``duration_s``; batch sizes log-uniform in [1, max_batch]
+    (floor(exp(U(0, ln(max_batch+1))))); each batch is the reads
+    [start, start+size) of a pool of ``pool`` reads, start uniform."""
+    rng = np.random.default_rng(seed)
+    n = max(1, int(duration_s * rate * 1.5) + 16)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    t = t[t < duration_s]
+    size = np.floor(np.exp(rng.uniform(0.0, np.log(max_batch + 1), len(t)))).astype(np.int64)
+    size = np.clip(size, 1, max_batch)
+    start = (rng.random(len(t)) * (pool - size + 1)).astype(np.int64)
+    return dict(t=t, size=size, start=start)

@@ -49,3 +49,32 @@ def test_binding_rejects_host_tensors_before_any_device_call():
 
     with pytest.raises(ValueError):
         grim._dptr(torch.zeros(4, dtype=torch.uint8), "ref", 1)
+
+
+def test_index_file_errors_without_gpu(tmp_path):
+    """grim_load checks the file before any device call: a missing file is an
+    I/O error, a file that is not an index (or a truncated header) a format
+    error, and a bad flag an argument error."""
+    from paper_1708_04329_gb300 import grim
+
+    with pytest.raises(grim.GrimError) as ei:
+        grim.grim_load(tmp_path / "missing.grim")
+    assert ei.value.code == grim.GRIM_E_IO
+    junk = tmp_path / "junk.grim"
+    junk.write_bytes(b"not an index" * 40)
+    with pytest.raises(grim.GrimError) as ei:
+        grim.grim_load(junk)
+    assert ei.value.code == grim.GRIM_E_FORMAT
+    junk.write_bytes(b"GRIMIDX1")
+    with pytest.raises(grim.GrimError) as ei:
+        grim.grim_load(junk)
+    assert ei.value.code == grim.GRIM_E_FORMAT
+    h = C_void()
+    assert grim._lib().grim_load(str(junk).encode(), 0, 2, h) == grim.GRIM_E_ARG
+    assert grim._lib().grim_load(str(junk).encode(), 8, 0, h) == grim.GRIM_E_ARG
+
+
+def C_void():
+    import ctypes
+
+    return ctypes.byref(ctypes.c_void_p())
