@@ -52,6 +52,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--cand-unroll", type=int, default=0,
+                   help="ragged workload: candidate gathers in flight (0 = autotune)")
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="serve workload: length of the measured arrival trace")
     p.add_argument("--workload", default="human", choices=["human", "finer", "ragged", "serve"],
@@ -85,6 +87,29 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(base: int, rank: int) -> int:
+    """Seed of rank `rank`'s reads: rank 0 keeps the workload's own seed, so a
+    1-GPU run filters exactly the single-GPU workload; other ranks get their
+    own reads (weak scaling: every rank filters a full batch)."""
+    return base + 7919 * rank
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The step time of the slowest rank (the job is done when it is)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_value(units_per_rank: int, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return units_per_rank * world / (ms_per_step / 1e3)
+
+
 def workload(args, rank: int):
     from paper_1708_04329_gb300 import synth
 
@@ -93,12 +118,12 @@ def workload(args, rank: int):
     if args.workload == "finer":
         w = synth.finer_index(n_reads=args.reads, g=g)
         if rank:  # other ranks: their own reads (weak scaling)
-            w["reads"] = synth.reads(g, args.reads, seed=5 + 7919 * rank, lengths=(150,), e=7,
+            w["reads"] = synth.reads(g, args.reads, seed=rank_seed(5, rank), lengths=(150,), e=7,
                                      max_edits=7)
     else:
         w = synth.human_exhaustive(n_reads=args.reads, g=g)
         if rank:
-            w["reads"] = synth.reads(g, args.reads, seed=3 + 7919 * rank, lengths=(100,), e=5,
+            w["reads"] = synth.reads(g, args.reads, seed=rank_seed(3, rank), lengths=(100,), e=5,
                                      max_edits=5)
     nb = (len(g) + w["B"] - 1) // w["B"]
     off, cand = synth.candidates((w["reads"].true_pos // w["B"]).astype(np.int32), nb,
@@ -262,11 +287,7 @@ def run_native(args, rank, world, local):
         torch.cuda.synchronize()
     prof = grim.grim_profile_get()
     grim.grim_profile(False)
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     clocks = clk.summary()
 
     # dominant kernel: the all-bins accumulate-and-threshold pass (over
@@ -308,7 +329,7 @@ def run_native(args, rank, world, local):
                 "coarse_survivors": stats["survivors"]}
     stages = {k: round(v[1] / max(v[0], 1), 3) for k, v in prof.items()}
     launches = int(sum(v[0] for v in prof.values()))
-    value = rs.n * world / (ms / args.steps / 1e3)
+    value = weak_value(rs.n, world, ms / args.steps)
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
@@ -458,7 +479,7 @@ def run_ragged(args, rank, world, local):
     g = synth.human_genome(args.genome)
     w = synth.ragged_candidates(n_reads=n_reads, g=g)
     if rank:
-        w["reads"] = synth.reads(g, n_reads, seed=4 + 7919 * rank, lengths=(100, 150, 250),
+        w["reads"] = synth.reads(g, n_reads, seed=rank_seed(4, rank), lengths=(100, 150, 250),
                                  probs=(0.5, 0.3, 0.2), e_frac=(5, 100), max_edits=None)
         nb0 = (len(g) + w["B"] - 1) // w["B"]
         w["cand_off"], w["cand"] = synth.candidates(
@@ -483,7 +504,8 @@ def run_ragged(args, rank, world, local):
     sample = dict(reads=dev["reads"][: int(rs.offsets[ns - 1] + rs.lens[ns - 1])],
                   offsets=dev["offsets"][:ns], lens=dev["lens"][:ns], e=dev["e"][:ns],
                   cand=dev["cand"][:cs], cand_off=dev["cand_off"][: ns + 1])
-    tuned = autotune.tune_candidate_unroll(idx, sample, max_e, cache=None)
+    tuned = (autotune.tune_candidate_unroll(idx, sample, max_e, cache=None) if not args.cand_unroll
+             else {"unroll": args.cand_unroll, "ms": None})
     cap = 4 * rs.n + 4096
     plan = grim.grim_plan_create(idx, max_reads=rs.n, max_bases=len(rs.seq), max_e=max_e, cap=cap,
                                  max_cand=n_cand, candidates=True, cand_unroll=tuned["unroll"])
@@ -531,13 +553,10 @@ def run_ragged(args, rank, world, local):
     except (OSError, ValueError):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     line = {
         "metric": "reads/s, candidate lists of ragged reads (graph-captured plan)",
-        "value": round(rs.n * world / (ms / 1e3), 1), "unit": UNIT, "n_gpus": world,
+        "value": round(weak_value(rs.n, world, ms), 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",

@@ -436,6 +436,15 @@ void grim_server_free(grim_server* s);
 
 /* ---- helpers of the mapper around the filter (§GRIM-Filter, Fig. 5) ----- */
 
+/* Reverse complement of reads (device pointers, grim_filter's layout): `out`
+ * receives, at the same offsets, each read reversed with A<->T and C<->G in
+ * either case (case kept; any other byte is moved unchanged).  The filter
+ * reads the forward strand only; a mapper that tests both strands submits
+ * these as further reads.  `out` must not overlap `reads`.  Asynchronous on
+ * `stream`.  Errors: GRIM_E_ARG, GRIM_E_CUDA. */
+int grim_reverse_complement(const char* reads, const uint64_t* offsets, const uint32_t* lens,
+                            uint32_t n_reads, char* out, void* stream);
+
 /* Bin whose core holds reference position `loc`: loc / B. */
 uint64_t grim_loc_to_bin(const grim_index* idx, uint64_t loc);
 

@@ -542,6 +542,15 @@ int grim_filter_host(const grim_index* idx, const char* reads, const uint64_t* o
   return rc;
 }
 
+int grim_reverse_complement(const char* reads, const uint64_t* offsets, const uint32_t* lens,
+                            uint32_t n_reads, char* out, void* stream) {
+  if (n_reads == 0) return GRIM_OK;
+  if (!reads || !offsets || !lens || !out || out == reads) return GRIM_E_ARG;
+  launch_reverse_complement(reads, offsets, lens, n_reads, out, static_cast<cudaStream_t>(stream));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GRIM_OK : cuda_fail(e);
+}
+
 uint64_t grim_loc_to_bin(const grim_index* idx, uint64_t loc) { return idx ? loc / idx->v.B : 0; }
 
 uint32_t grim_edits_for_rate(uint32_t L, uint32_t num, uint32_t den) {

@@ -112,6 +112,8 @@ void launch_row_popcount(const uint32_t* tm, uint32_t rows, uint64_t words_per_r
 
 // max_e: reads with a larger budget are an argument error (graph launches
 // fix the counter depth from it); 0xFFFF = no limit
+void launch_reverse_complement(const char* reads, const uint64_t* offsets, const uint32_t* lens,
+                               uint32_t n_reads, char* out, cudaStream_t st);
 // max_bases: size of the reads buffer when known (a read ending past it
 // fails the batch with kStatusArg), else ~0
 void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t* lens,

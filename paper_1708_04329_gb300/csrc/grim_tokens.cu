@@ -104,7 +104,38 @@ __global__ void k_check_candidates(const int32_t* __restrict__ cand,
   if (i == 0 && cand_off[n_reads] != n_cand) atomicOr(&ctl->status, kStatusBadCsr);
 }
 
+// Reverse complement, one warp per read: out[off + L-1-j] = comp(reads[off + j])
+// with A<->T and C<->G in either case (case kept); other bytes unchanged.
+__global__ void k_reverse_complement(const char* __restrict__ reads,
+                                     const uint64_t* __restrict__ offsets,
+                                     const uint32_t* __restrict__ lens, uint32_t n_reads,
+                                     char* __restrict__ out) {
+  const uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (r >= n_reads) return;
+  const uint64_t off = offsets[r];
+  const uint32_t L = lens[r];
+  for (uint32_t j = lane; j < L; j += 32) {
+    const uint32_t c = (uint8_t)reads[off + j];
+    const uint32_t u = c & 0xDFu, low = c & 0x20u;
+    uint32_t d = c;
+    if (u == 0x41u) d = 0x54u | low;       // A -> T
+    else if (u == 0x54u) d = 0x41u | low;  // T -> A
+    else if (u == 0x43u) d = 0x47u | low;  // C -> G
+    else if (u == 0x47u) d = 0x43u | low;  // G -> C
+    out[off + L - 1 - j] = (char)d;
+  }
+}
+
 }  // namespace
+
+void launch_reverse_complement(const char* reads, const uint64_t* offsets, const uint32_t* lens,
+                               uint32_t n_reads, char* out, cudaStream_t st) {
+  if (n_reads == 0) return;
+  const uint32_t threads = 256;
+  const uint64_t grid = ((uint64_t)n_reads * 32 + threads - 1) / threads;
+  k_reverse_complement<<<(unsigned)grid, threads, 0, st>>>(reads, offsets, lens, n_reads, out);
+}
 
 void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t* lens,
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,

@@ -51,6 +51,7 @@ EXPORTS = (
     "grim_plan_wait", "grim_plan_device_bytes", "grim_plan_free", "grim_default_coarse_factor",
     "grim_server_create", "grim_server_submit", "grim_server_wait", "grim_server_take",
     "grim_server_stats_get", "grim_server_free", "grim_save", "grim_load",
+    "grim_reverse_complement",
 )
 
 
@@ -180,6 +181,8 @@ def _lib() -> C.CDLL:
         lib.grim_plan_free.restype = None
         lib.grim_plan_free.argtypes = [vp]
         lib.grim_profile.restype = i32
+        lib.grim_reverse_complement.restype = i32
+        lib.grim_reverse_complement.argtypes = [vp, vp, vp, u32, vp, vp]
         lib.grim_save.restype = i32
         lib.grim_save.argtypes = [vp, C.c_char_p]
         lib.grim_load.restype = i32
@@ -539,6 +542,49 @@ def grim_filter(index: GrimIndex, reads, offsets, lens, e, cand=None, cand_off=N
         raise err
     n = int(n_out.value)
     return out[0][:n], out[1][:n], out[2][:n]
+
+
+def grim_filter_count(index: GrimIndex, reads, offsets, lens, e, cand=None, cand_off=None,
+                      workspace: Workspace | None = None, stream=None) -> int:
+    """Number of passing (read, bin) pairs, without the pass list (a
+    grim_filter call with no output capacity)."""
+    n_reads = int(lens.numel())
+    n_cand = int(cand.numel()) if cand is not None else 0
+    ws = workspace or Workspace()
+    ws.ensure(grim_filter_workspace_size(index, n_reads, n_cand, 0))
+    n_out = C.c_uint64(0)
+    rc = _lib().grim_filter(
+        index.handle, _dptr(reads, "reads", 1) if reads.numel() else 0, _dptr(offsets, "offsets", 8),
+        _dptr(lens, "lens", 4), n_reads, _dptr(e, "e", 2), _dptr(cand, "cand", 4),
+        _dptr(cand_off, "cand_off", 8), n_cand, None, None, None, 0, C.byref(n_out),
+        ws.ptr(), ws.nbytes(), _stream_ptr(stream))
+    if rc not in (GRIM_OK, GRIM_E_OVERFLOW):
+        raise GrimError(rc, "grim_filter")
+    return int(n_out.value)
+
+
+def grim_reverse_complement(reads, offsets, lens, out=None, stream=None):
+    """Reverse complements of CUDA-resident reads, at the same offsets."""
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(reads)
+    rc = _lib().grim_reverse_complement(
+        _dptr(reads, "reads", 1) if reads.numel() else 0, _dptr(offsets, "offsets", 8),
+        _dptr(lens, "lens", 4), int(lens.numel()), _dptr(out, "out", 1) if out.numel() else 0,
+        _stream_ptr(stream))
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_reverse_complement")
+    return out
+
+
+def both_strands(reads, offsets, lens, e):
+    """A batch of 2n reads for filtering both strands: reads 0..n-1 as given,
+    read n+i the reverse complement of read i (same length and budget)."""
+    torch = _torch()
+    rc = grim_reverse_complement(reads, offsets, lens)
+    nb = int(reads.numel())
+    return dict(reads=torch.cat([reads, rc]), offsets=torch.cat([offsets, offsets + nb]),
+                lens=torch.cat([lens, lens]), e=torch.cat([e, e]))
 
 
 def grim_filter_host(index: GrimIndex, reads, offsets, lens, e, cand=None, cand_off=None,

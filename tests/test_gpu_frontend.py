@@ -1,0 +1,85 @@
+"""Mapper front-end helpers on the GPU: reverse complements, both-strand
+batches, count-only filtering and the read-existence measure of the
+parameter sweep, each against the oracle or a plain restatement."""
+import numpy as np
+import pytest
+
+import oracle
+from tests.conftest import Reads
+from tests.gpu_helpers import assert_same, build, dev_reads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+COMP = bytes.maketrans(b"ACGTacgt", b"TGCAtgca")
+
+
+@pytest.fixture(scope="module")
+def world():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_1708_04329_gb300 import synth
+
+    g = synth.human_genome(300_000, seed=91)
+    return g, oracle.bin_vectors(g, 100, 5, 100), build(g, 100, 5, 100, 7)
+
+
+def _host(t):
+    return t.cpu().numpy().view(np.uint32) if t.dtype != torch.uint8 else t.cpu().numpy()
+
+
+def test_reverse_complement_matches_plain_restatement():
+    from paper_1708_04329_gb300 import grim
+
+    rng = np.random.default_rng(3)
+    strs = ["".join(rng.choice(list("ACGTacgtN-"), int(n))) for n in rng.integers(0, 300, 200)]
+    rs = Reads(strs, [0] * len(strs))
+    kw = dev_reads(rs)
+    out = grim.grim_reverse_complement(kw["reads"], kw["offsets"], kw["lens"])
+    got = out.cpu().numpy().tobytes()
+    want = b"".join(s.encode().translate(COMP)[::-1] for s in strs)
+    assert got == want
+
+
+def test_both_strands_filter(world):
+    from paper_1708_04329_gb300 import grim, synth
+
+    g, oix, idx = world
+    rs = synth.reads(g, 400, seed=92, lengths=(100,), e=4, max_edits=4)
+    strs = [rs.read(i).decode() for i in range(rs.n)]
+    rc = [s.encode().translate(COMP)[::-1].decode() for s in strs]
+    both = Reads(strs + rc, list(rs.e) * 2)
+    kw = grim.both_strands(**dev_reads(rs))
+    got = tuple(_host(x) for x in grim.grim_filter(idx, **kw))
+    assert_same(got, oracle.filter(oix, both))
+
+
+def test_count_and_existence(world):
+    from paper_1708_04329_gb300 import existence, grim, synth
+
+    g, oix, idx = world
+    rs = synth.reads(g, 300, seed=93, lengths=(100,), e=3, max_edits=3)
+    want = oracle.filter(oix, rs)
+    kw = dev_reads(rs)
+    assert grim.grim_filter_count(idx, **kw) == len(want[0])
+    assert existence.read_existence(idx, kw) == len(want[0]) / (rs.n * oix.num_bins)
+    # T <= 0: every bin passes
+    kw["e"] = torch.full_like(kw["e"], 30)
+    assert grim.grim_filter_count(idx, **kw) == rs.n * oix.num_bins
+
+
+def test_existence_sweep_small(world):
+    from paper_1708_04329_gb300 import existence
+
+    g, _, _ = world
+    rows = existence.sweep(g, qs=(4, 5), bins_k=(1,), rates_pct=(0, 3), n_sets=2,
+                           reads_per_set=100, max_edits=0)
+    assert len(rows) == 4
+    for r in rows:
+        assert 0 < r["min"] <= r["mean"] <= r["max"] <= 1
+    # more tolerance never lowers existence; longer tokens never raise it
+    by = {(r["q"], r["rate_pct"]): r["mean"] for r in rows}
+    assert by[(4, 3)] >= by[(4, 0)] and by[(5, 3)] >= by[(5, 0)]
+    assert by[(5, 0)] <= by[(4, 0)]
