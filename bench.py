@@ -499,7 +499,7 @@ def run_ragged(args, rank, world, local):
     n_cand = len(w["cand"])
     max_e = int(rs.e.max())
     # autotune the read tile on a sample of the batch
-    ns = min(rs.n, 200_000)
+    ns = min(rs.n, 1_000_000)
     cs = int(w["cand_off"][ns])
     sample = dict(reads=dev["reads"][: int(rs.offsets[ns - 1] + rs.lens[ns - 1])],
                   offsets=dev["offsets"][:ns], lens=dev["lens"][:ns], e=dev["e"][:ns],

@@ -348,9 +348,11 @@ void grim_free(grim_index* idx) {
 
 uint64_t grim_filter_workspace_size(const grim_index* idx, uint32_t n_reads, uint64_t n_cand,
                                     uint64_t cap) {
-  (void)n_cand;
   if (!idx) return 0;
-  return layout(idx->v, n_reads, cap, two_level_capable(idx) ? idx->factor : 0).total;
+  // all-bins mode needs at least as much as candidate mode
+  return layout(idx->v, n_reads, cap, two_level_capable(idx) ? idx->factor : 0,
+                token_copies(idx->v, n_cand > 0))
+      .total;
 }
 
 int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offsets,
@@ -372,7 +374,8 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   if (cap > 0xFFFFFFFFull) return GRIM_E_ARG;
   const IndexView& v = idx->v;
   const uint32_t f = capable ? idx->factor : 0;
-  const Layout L = layout(v, n_reads, cap, f);
+  const uint32_t copies = token_copies(v, cand_mode);
+  const Layout L = layout(v, n_reads, cap, f, copies);
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return GRIM_E_ARG;
   if (workspace_bytes < L.total) return GRIM_E_WORKSPACE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -387,7 +390,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
                  reinterpret_cast<uint8_t*>(ws + L.cnt_a), rcap};
   RecordsView rb{reinterpret_cast<unsigned long long*>(ws + L.keys_b),
                  reinterpret_cast<uint8_t*>(ws + L.cnt_b), rcap};
-  ReadsView rv{tokens, meta, n_reads, token_stride(v)};
+  ReadsView rv{tokens, meta, n_reads, token_stride(v), copies};
   const uint32_t bin_bits = v.num_bins > 1 ? bit_length(v.num_bins - 1) : 0;
   uint64_t survivors = 0;
   const uint32_t read_bits = n_reads > 1 ? bit_length((uint64_t)n_reads - 1) : 0;

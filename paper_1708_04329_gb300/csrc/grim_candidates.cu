@@ -4,10 +4,13 @@
 //
 // GB300 mapping
 // -------------
-// * One warp per read (taken from a global counter).  The read's tokens are
-//   turned into a multiplicity histogram (a byte per token value) and then
-//   into bit planes P_k = {t : bit k of mult(t) is 1}, held in registers, so
-//   that for any bin vector v the token sum is
+// * Warps claim chunks of 256-4096 consecutive candidates of the flattened lists
+//   from a global counter (a chunk may hold many short lists; a long list is
+//   spread over many warps, so no single 20,000-candidate list is left
+//   running alone at the end).  For each read in its chunk the warp turns the
+//   read's tokens into a multiplicity histogram (a byte per token value) and
+//   then into bit planes P_k = {t : bit k of mult(t) is 1}, held in
+//   registers, so that for any bin vector v the token sum is
 //       sum = sum_k 2^k * popcount(v & P_k)
 //   -- every position counts, repeats included, with a handful of AND +
 //   POPC per 32 bits instead of one bit test per token.
@@ -63,6 +66,93 @@ __host__ __device__ constexpr uint32_t warp_smem_words(uint32_t r4, uint32_t wpb
   return hist_words_of(r4) + (8 - kRegPlanes) * wpb;
 }
 
+// The read's multiplicity histogram (byte t = how many of its positions hold
+// token t) and its bit planes P_k = {t : bit k of mult(t)} for this lane's WL
+// words of a bin vector: planes below kRegPlanes in registers, the rest in
+// shared memory (xplanes[k - kRegPlanes][word]).  Returns K, the number of
+// planes in use, and the read's threshold in *thr.  Warp-collective.
+template <int WPB, int WL>
+__device__ __forceinline__ uint32_t build_planes(const ReadsView& rv, uint32_t r, uint32_t r4,
+                                                 uint32_t* hist, uint32_t* xplanes, uint32_t lane,
+                                                 uint32_t sub, uint32_t (&P)[kRegPlanes][WL],
+                                                 uint32_t* thr) {
+  const uint32_t hist_words = hist_words_of(r4);
+  // the warp has finished reading the previous read's histogram
+  __syncwarp();
+  for (uint32_t i = lane; i < hist_words; i += 32) hist[i] = 0;
+  __syncwarp();
+  const uint32_t m = rv.meta[r];
+  const uint32_t ntok = m & 0xFFu, dmax = (m >> 8) & 0xFFu;
+  const uint16_t* tk = rv.tokens + (uint64_t)r * rv.copies * rv.ts;
+  for (uint32_t j = lane; j < ntok; j += 32) {
+    const uint32_t t = tk[j];
+    if (t < r4) atomicAdd(hist + (t >> 2), 1u << (8 * (t & 3u)));
+  }
+  __syncwarp();
+  // the largest multiplicity decides how many bit planes the sums need
+  // (almost always 1 or 2)
+  uint32_t mx = 0;
+  for (uint32_t i = lane; i < hist_words; i += 32) {
+    const uint32_t h = hist[i];
+    mx = max(mx, max(max(h & 0xFFu, (h >> 8) & 0xFFu), max((h >> 16) & 0xFFu, h >> 24)));
+  }
+  mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+  const uint32_t K = 32 - __clz(mx);  // planes in use
+#pragma unroll
+  for (int w = 0; w < WL; ++w) {
+    const uint32_t wi = sub * WL + w;  // word index in the vector: tokens wi*32 .. wi*32+31
+    uint32_t hw[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t h = wi * 8 + j;
+      hw[j] = h < hist_words && (wi * 32 + 4 * j) < r4 ? hist[h] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if ((uint32_t)k < K) {
+        uint32_t pk = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          uint32_t x = (hw[j] >> k) & 0x01010101u;  // bit k of 4 byte counters
+          x |= x >> 7;
+          x |= x >> 14;
+          pk |= (x & 0xFu) << (4 * j);
+        }
+        if (k < kRegPlanes) P[k < kRegPlanes ? k : 0][w] = pk;
+        else xplanes[(k - kRegPlanes) * WPB + wi] = pk;
+      } else if (k < kRegPlanes) {
+        P[k < kRegPlanes ? k : 0][w] = 0;
+      }
+    }
+  }
+  *thr = ntok - dmax;  // pass iff sum >= (L-q+1) - min(q*e, L-q+1)
+  return K;
+}
+
+// sum_k 2^k popc(v & P_k) over this lane's WL words
+template <int WPB, int WL>
+__device__ __forceinline__ uint32_t plane_sum(const uint32_t (&v)[WL],
+                                              const uint32_t (&P)[kRegPlanes][WL], uint32_t K,
+                                              const uint32_t* xplanes, uint32_t sub) {
+  uint32_t sum = 0;
+#pragma unroll
+  for (int p = 0; p < kRegPlanes; ++p) {
+    if ((uint32_t)p < K) {
+      uint32_t s = 0;
+#pragma unroll
+      for (int w = 0; w < WL; ++w) s += __popc(v[w] & P[p][w]);
+      sum += s << p;
+    }
+  }
+  for (uint32_t p = kRegPlanes; p < K; ++p) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < WL; ++w) s += __popc(v[w] & xplanes[(p - kRegPlanes) * WPB + sub * WL + w]);
+    sum += s << p;
+  }
+  return sum;
+}
+
 template <int U, int CPW>
 __device__ __forceinline__ void load_ids(const int32_t* __restrict__ cand, uint64_t kb, uint64_t c1,
                                          uint32_t slot, uint32_t (&b)[U]) {
@@ -73,148 +163,125 @@ __device__ __forceinline__ void load_ids(const int32_t* __restrict__ cand, uint6
   }
 }
 
+// Candidates per work claim: large enough that the search for a chunk's
+// first read and the planes of the reads split at chunk edges stay cheap,
+// small enough that every warp gets about 16 chunks (an even finish).
+constexpr uint64_t kChunkMin = 256, kChunkMax = 4096, kChunksPerWarp = 16;
+__device__ __forceinline__ uint64_t chunk_size(uint64_t n_cand, uint64_t warps) {
+  uint64_t c = kChunkMax;
+  while (c > kChunkMin && c * kChunksPerWarp * warps > n_cand) c >>= 1;
+  return c;
+}
+
+// The read holding candidate x: the largest r < n_reads with cand_off[r] <= x
+// (empty lists in between are skipped), by a 32-way search.
+__device__ __forceinline__ uint32_t read_of(const uint64_t* __restrict__ cand_off, uint32_t n_reads,
+                                            uint64_t x, uint32_t lane) {
+  uint32_t lo = 0, hi = n_reads;  // cand_off[lo] <= x < cand_off[hi]
+  while (hi - lo > 1) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t p = lo + lane * step;
+    const bool le = p < hi && cand_off[p] <= x;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, le);  // lane 0 always (cand_off[lo] <= x)
+    const uint32_t last = 31 - __clz(bal);
+    lo = lo + last * step;
+    hi = min(hi, lo + step);
+  }
+  return lo;
+}
+
 template <int WPB, int U>
-__global__ void __launch_bounds__(kWarps * 32) k_candidates(CandArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, 4) k_candidates(CandArgs a) {
   using C = Cfg<WPB>;
   constexpr int WL = C::WL, G = C::G, CPW = C::CPW;
   extern __shared__ uint32_t s_warp[];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t r4 = a.ix.r4;
-  const uint32_t hist_words = hist_words_of(r4);
   uint32_t* hist = s_warp + warp * warp_smem_words(r4, WPB);  // byte t = multiplicity of token t
-  uint32_t* xplanes = hist + hist_words;                        // [8 - kRegPlanes][WPB]
+  uint32_t* xplanes = hist + hist_words_of(r4);                 // [8 - kRegPlanes][WPB]
   const uint32_t sub = lane % G;     // this lane's slice of a bin vector
   const uint32_t slot = lane / G;    // which of the warp's CPW candidates
   if (*(volatile uint32_t*)&a.ctl->status) return;
   if (gated_off(a.ctl, a.live)) return;  // the batch takes the other path
   const uint32_t n_reads = live_reads(a.ctl, a.live, a.rv.n_reads);
+  if (n_reads == 0) return;
+  // the batch's lists span candidates [c_begin, c_end); warps claim chunks
+  // of `chunk` consecutive candidates, so a long list is shared by many warps
+  const uint64_t c_begin = a.cand_off[0], c_end = a.cand_off[n_reads];
+  const uint64_t chunk =
+      c_end > c_begin ? chunk_size(c_end - c_begin, (uint64_t)gridDim.x * kWarps) : kChunkMin;
+  const uint64_t n_chunks = c_end > c_begin ? (c_end - c_begin + chunk - 1) / chunk : 0;
 
-  // the next read is claimed one read ahead, so the atomic's latency overlaps
-  // the current read's work
-  uint32_t r_next = 0;
-  if (lane == 0) r_next = atomicAdd(&a.ctl->item, 1u);
+  uint32_t cur = 0xFFFFFFFFu, K = 0, thr = 0;  // the read whose planes are built
+  uint32_t P[kRegPlanes][WL];
+  // the next chunk is claimed one chunk ahead, so the atomic's latency
+  // overlaps the current chunk's work
+  uint32_t cj_next = 0;
+  if (lane == 0) cj_next = atomicAdd(&a.ctl->item, 1u);
   for (;;) {
-    const uint32_t r = __shfl_sync(0xFFFFFFFFu, r_next, 0);
-    if (r >= n_reads) break;
-    if (lane == 0) r_next = atomicAdd(&a.ctl->item, 1u);
-    const uint64_t c0 = a.cand_off[r], c1 = a.cand_off[r + 1];
-    if (c0 == c1) continue;
-    // the first candidate ids are fetched while the histogram is built
-    uint32_t bc[U];
-    load_ids<U, CPW>(a.cand, c0, c1, slot, bc);
-
-    // multiplicity histogram of the read's clean tokens (the warp has
-    // finished reading the previous read's histogram)
-    __syncwarp();
-    for (uint32_t i = lane; i < hist_words; i += 32) hist[i] = 0;
-    __syncwarp();
-    const uint32_t m = a.rv.meta[r];
-    const uint32_t ntok = m & 0xFFu, dmax = (m >> 8) & 0xFFu;
-    const uint16_t* tk = a.rv.tokens + (uint64_t)r * a.rv.ts;
-    for (uint32_t j = lane; j < ntok; j += 32) {
-      const uint32_t t = tk[j];
-      if (t < r4) atomicAdd(hist + (t >> 2), 1u << (8 * (t & 3u)));
-    }
-    __syncwarp();
-
-    // the largest multiplicity decides how many bit planes the sums need
-    // (almost always 1 or 2)
-    uint32_t mx = 0;
-    for (uint32_t i = lane; i < hist_words; i += 32) {
-      const uint32_t h = hist[i];
-      mx = max(mx, max(max(h & 0xFFu, (h >> 8) & 0xFFu), max((h >> 16) & 0xFFu, h >> 24)));
-    }
-    mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-    const uint32_t K = 32 - __clz(mx);  // planes in use
-    // bit planes k < K of the multiplicities for this lane's WL words: the
-    // first kRegPlanes in registers, the rest (rare) in shared memory
-    uint32_t P[kRegPlanes][WL];
-#pragma unroll
-    for (int w = 0; w < WL; ++w) {
-      const uint32_t wi = sub * WL + w;  // word index in the vector: tokens wi*32 .. wi*32+31
-      uint32_t hw[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const uint32_t h = wi * 8 + j;
-        hw[j] = h < hist_words && (wi * 32 + 4 * j) < r4 ? hist[h] : 0u;
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if ((uint32_t)k < K) {
-          uint32_t pk = 0;
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            uint32_t x = (hw[j] >> k) & 0x01010101u;  // bit k of 4 byte counters
-            x |= x >> 7;
-            x |= x >> 14;
-            pk |= (x & 0xFu) << (4 * j);
-          }
-          if (k < kRegPlanes) P[k < kRegPlanes ? k : 0][w] = pk;
-          else xplanes[(k - kRegPlanes) * WPB + wi] = pk;
-        } else if (k < kRegPlanes) {
-          P[k < kRegPlanes ? k : 0][w] = 0;
+    const uint32_t cj = __shfl_sync(0xFFFFFFFFu, cj_next, 0);
+    if (cj >= n_chunks) break;
+    if (lane == 0) cj_next = atomicAdd(&a.ctl->item, 1u);
+    uint64_t pk = c_begin + (uint64_t)cj * chunk;
+    const uint64_t ce = min(pk + chunk, c_end);
+    uint32_t r = read_of(a.cand_off, n_reads, pk, lane);
+    uint64_t re = a.cand_off[r + 1];
+    while (pk < ce) {
+      // the segment [pk, c1) of read r's list inside this chunk
+      const uint64_t c1 = min(re, ce);
+      // the end of the next read's list is fetched while this one is scored
+      const uint64_t re_next = r + 2 <= n_reads && c1 < ce ? a.cand_off[r + 2] : re;
+      if (c1 > pk) {
+        // the first candidate ids are fetched while the planes are built
+        uint32_t bc[U];
+        load_ids<U, CPW>(a.cand, pk, c1, slot, bc);
+        if (r != cur) {
+          cur = r;
+          K = build_planes<WPB, WL>(a.rv, r, r4, hist, xplanes, lane, sub, P, &thr);
         }
-      }
-    }
-    if (K > kRegPlanes) __syncwarp();
-    const uint32_t thr = ntok - dmax;   // pass iff sum >= (L-q+1) - min(q*e, L-q+1)
-
-    // U independent gathers in flight per lane group; the ids of the next
-    // step are fetched before this step's vectors are used
-    for (uint64_t kb = c0; kb < c1; kb += (uint64_t)CPW * U) {
-      uint32_t bn[U];
-      load_ids<U, CPW>(a.cand, kb + (uint64_t)CPW * U, c1, slot, bn);
-      uint32_t v[U][WL];
+        // U independent gathers in flight per lane group; the ids of the
+        // next step are fetched before this step's vectors are used
+        for (uint64_t kb = pk; kb < c1; kb += (uint64_t)CPW * U) {
+          uint32_t bn[U];
+          load_ids<U, CPW>(a.cand, kb + (uint64_t)CPW * U, c1, slot, bn);
+          uint32_t v[U][WL];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (kb + (uint64_t)u * CPW + slot < c1)
-          load_words<WL>(a.ix.bm + (uint64_t)bc[u] * WPB + sub * WL, v[u]);
-      }
+          for (int u = 0; u < U; ++u) {
+            if (kb + (uint64_t)u * CPW + slot < c1)
+              load_words<WL>(a.ix.bm + (uint64_t)bc[u] * WPB + sub * WL, v[u]);
+          }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint64_t k = kb + (uint64_t)u * CPW + slot;
-        const bool valid = k < c1;
-        uint32_t sum = 0;
-        if (valid) {
+          for (int u = 0; u < U; ++u) {
+            const uint64_t k = kb + (uint64_t)u * CPW + slot;
+            const bool valid = k < c1;
+            uint32_t sum = valid ? plane_sum<WPB, WL>(v[u], P, K, xplanes, sub) : 0u;
 #pragma unroll
-          for (int p = 0; p < kRegPlanes; ++p) {
-            if ((uint32_t)p < K) {
-              uint32_t s = 0;
-#pragma unroll
-              for (int w = 0; w < WL; ++w) s += __popc(v[u][w] & P[p][w]);
-              sum += s << p;
+            for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+            // bins past num_bins exist only as zero padding of the table
+            // (members of the last super-bin); they never pass
+            const bool real = valid && bc[u] < a.ix.num_bins;
+            const bool pass = real && sub == 0 && sum >= thr;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
+            if (bal) {
+              unsigned long long base = 0;
+              if (lane == 0) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)__popc(bal));
+              base = __shfl_sync(0xFFFFFFFFu, base, 0);
+              if (pass) {
+                const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+                if (pos < a.rec.cap) {
+                  a.rec.keys[pos] = k;
+                  a.rec.counts[pos] = (uint8_t)sum;
+                }
+              }
             }
           }
-          for (uint32_t p = kRegPlanes; p < K; ++p) {
-            uint32_t s = 0;
 #pragma unroll
-            for (int w = 0; w < WL; ++w)
-              s += __popc(v[u][w] & xplanes[(p - kRegPlanes) * WPB + sub * WL + w]);
-            sum += s << p;
-          }
-        }
-#pragma unroll
-        for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-        // bins past num_bins exist only as zero padding of the table (members
-        // of the last super-bin); they never pass
-        const bool real = valid && bc[u] < a.ix.num_bins;
-        const bool pass = real && sub == 0 && sum >= thr;
-        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
-        if (bal) {
-          unsigned long long base = 0;
-          if (lane == 0) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)__popc(bal));
-          base = __shfl_sync(0xFFFFFFFFu, base, 0);
-          if (pass) {
-            const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
-            if (pos < a.rec.cap) {
-              a.rec.keys[pos] = k;
-              a.rec.counts[pos] = (uint8_t)sum;
-            }
-          }
+          for (int u = 0; u < U; ++u) bc[u] = bn[u];
         }
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) bc[u] = bn[u];
+      pk = c1;
+      ++r;
+      re = re_next;
     }
   }
 }
@@ -227,10 +294,8 @@ void launch_u(const CandArgs& a, cudaStream_t st, const char* name) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_candidates<WPB, U>, kWarps * 32, smem);
   if (per_sm < 1) per_sm = 1;
-  uint64_t want = ((uint64_t)a.rv.n_reads + kWarps - 1) / kWarps;
-  uint64_t grid = (uint64_t)sms * per_sm;
-  if (grid > want) grid = want;
-  if (grid < 1) grid = 1;
+  // persistent: warps that find no chunk left exit at once
+  const uint64_t grid = (uint64_t)sms * per_sm;
   ProfScope ps(name, st);
   k_candidates<WPB, U><<<(unsigned)grid, kWarps * 32, smem, st>>>(a);
 }

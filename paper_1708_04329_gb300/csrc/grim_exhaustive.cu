@@ -213,6 +213,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
     asm volatile("st.shared.v4.u32 [%0], {%1,%1,%1,%1};" ::"r"(pad_tokens + tid * 16u), "r"(pp));
   }
   const uint32_t lane_base = sh_base + li * 16u;
+  // the token copy this group reads (block-rotated copies spread the groups'
+  // 32-byte rows over the bank groups at q = 6)
+  const uint32_t copy = a.rv.copies > 1 ? grp % a.rv.copies : 0u;
   const uint32_t row_chunks = a.rv.ts * 2u / 16u;  // 16-byte chunks of a token row
 
   for (;;) {
@@ -268,7 +271,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
       if (k < nr) {
         nxt = r0 + k;
         nxt_meta = __ldg(a.rv.meta + nxt);
-        const char* src = reinterpret_cast<const char*>(a.rv.tokens + (uint64_t)nxt * a.rv.ts);
+        const char* src = reinterpret_cast<const char*>(
+            a.rv.tokens + ((uint64_t)nxt * a.rv.copies + copy) * a.rv.ts);
         for (uint32_t ch = li; ch < row_chunks; ch += GL)
           asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(slot + ch * 16u),
                        "l"(src + ch * 16u));
@@ -307,7 +311,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
           nxt = k < nr ? r0 + k : kNone;
           if (nxt != kNone) {
             nxt_meta = __ldg(a.rv.meta + nxt);
-            const char* src = reinterpret_cast<const char*>(a.rv.tokens + (uint64_t)nxt * a.rv.ts);
+            const char* src = reinterpret_cast<const char*>(
+                a.rv.tokens + ((uint64_t)nxt * a.rv.copies + copy) * a.rv.ts);
             const uint32_t dst = slot + (buf ^ 1u) * a.row_stride;
             for (uint32_t ch = li; ch < row_chunks; ch += GL)
               asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst + ch * 16u),

@@ -83,12 +83,14 @@ struct IndexView {
   const uint32_t* presence;
 };
 
-// Reads after tokenising: tokens[r * ts + j], meta[r] = ntok | D' << 8 where
+// Reads after tokenising: token j of read r (copy k) at
+// tokens[(r * copies + k) * ts + j], meta[r] = ntok | D' << 8 where
 // D' = min(q*e, ntok) is the number of misses a passing bin may have.
 struct ReadsView {
-  const uint16_t* tokens;
+  const uint16_t* tokens;  // read r, copy k: tokens + (r * copies + k) * ts
   const uint32_t* meta;
   uint32_t n_reads, ts;
+  uint32_t copies;  // 1, or 4 block-rotated copies for the 256-bin tiles (q = 6)
 };
 
 struct RecordsView {
@@ -110,12 +112,12 @@ void launch_build_token_major(const uint32_t* codes, const uint32_t* invalid, co
 void launch_row_popcount(const uint32_t* tm, uint32_t rows, uint64_t words_per_row,
                          uint32_t* presence, cudaStream_t st);
 
-// max_e: reads with a larger budget are an argument error (graph launches
-// fix the counter depth from it); 0xFFFF = no limit
 void launch_reverse_complement(const char* reads, const uint64_t* offsets, const uint32_t* lens,
                                uint32_t n_reads, char* out, cudaStream_t st);
-// max_bases: size of the reads buffer when known (a read ending past it
-// fails the batch with kStatusArg), else ~0
+// max_e: reads with a larger budget are an argument error (graph launches
+// fix the counter depth from it); 0xFFFF = no limit.  max_bases: size of the
+// reads buffer when known (a read ending past it fails the batch with
+// kStatusArg), else ~0.  rv.copies token copies per read are written.
 void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t* lens,
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
                      uint32_t* meta, Ctl* ctl, cudaStream_t st, Live live = {false, 0},
@@ -198,12 +200,19 @@ inline uint64_t record_capacity(uint32_t n_reads, uint64_t cap, uint32_t coarse_
 
 // coarse_factor > 0: room for the coarse pass's survivors and for the
 // candidate lists they expand into (coarse_factor per survivor)
-inline Layout layout(const IndexView& v, uint32_t n_reads, uint64_t cap, uint32_t coarse_factor) {
+// Token copies per read: the all-bins kernel's 256-bin tiles (q = 6) read
+// one of 4 block-rotated copies per lane group (see k_tokenise).
+inline uint32_t token_copies(const IndexView& v, bool cand_mode) {
+  return !cand_mode && v.r4 > 1024 ? 4u : 1u;
+}
+
+inline Layout layout(const IndexView& v, uint32_t n_reads, uint64_t cap, uint32_t coarse_factor,
+                     uint32_t copies) {
   Layout L{};
   const uint64_t rcap = record_capacity(n_reads, cap, coarse_factor);
   uint64_t o = sizeof(Ctl);
   L.tok = o;
-  o = align256(o + (uint64_t)n_reads * token_stride(v) * sizeof(uint16_t));
+  o = align256(o + (uint64_t)n_reads * copies * token_stride(v) * sizeof(uint16_t));
   L.meta = o;
   o = align256(o + (uint64_t)n_reads * sizeof(uint32_t));
   L.keys_a = o;

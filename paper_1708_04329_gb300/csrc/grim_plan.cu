@@ -130,7 +130,7 @@ int capture(grim_plan* p) {
   RecordsView rb{reinterpret_cast<unsigned long long*>(ws + L.keys_b),
                  reinterpret_cast<uint8_t*>(ws + L.cnt_b), rcap};
   ReadsView rv{reinterpret_cast<uint16_t*>(ws + L.tok), reinterpret_cast<uint32_t*>(ws + L.meta),
-               d.max_reads, token_stride(v)};
+               d.max_reads, token_stride(v), token_copies(v, p->cand_mode)};
   const uint32_t bin_bits = v.num_bins > 1 ? bit_length(v.num_bins - 1) : 0;
   const uint32_t read_bits = d.max_reads > 1 ? bit_length((uint64_t)d.max_reads - 1) : 0;
   const bool has_exact = (idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR) != 0;
@@ -240,7 +240,7 @@ int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_pla
   p->cand_mode = cand_mode;
   p->hio = hio;
   p->f = (!cand_mode && two_level_capable(idx)) ? idx->factor : 0;
-  p->L = layout(idx->v, desc->max_reads, desc->cap, p->f);
+  p->L = layout(idx->v, desc->max_reads, desc->cap, p->f, token_copies(idx->v, cand_mode));
   const uint64_t n = desc->max_reads;
   const uint64_t mc = cand_mode ? desc->max_cand : 0;
   // one device allocation: inputs, outputs, then the workspace (256-aligned)

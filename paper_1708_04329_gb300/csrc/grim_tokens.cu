@@ -12,28 +12,41 @@ constexpr uint32_t kMaxStride = 256;  // token stride: <= 255 tokens rounded up 
 // One warp per read.  The read's tokens (row indices of the table: the token
 // value for a clean q-gram, rowInvalid for one holding a non-base -- it still
 // counts among the L-q+1 tokens and can never be found -- and rowPad after
-// the last token) are written to tokens[r*ts ...].  With a presence table
-// they are written rarest first -- q-grams with a non-base, which every bin
-// misses, then ascending number of (super-)bins holding the token, ties by
-// position -- so that the all-bins kernels see misses as early as possible;
-// a sum does not depend on the order.  meta[r] = ntok | D' << 8 with
-// D' = min(q*e, ntok): a bin passes iff at most D' of the read's tokens are
-// missing from it, which is sum >= (L-q+1) - q*e.
+// the last token) are written to tokens[(r*copies + k)*ts ...].  With a
+// presence table they are written rarest first -- q-grams with a non-base,
+// which every bin misses, then ascending number of (super-)bins holding the
+// token, ties by position -- so that the all-bins kernels see misses as early
+// as possible; a sum does not depend on the order.  meta[r] = ntok | D' << 8
+// with D' = min(q*e, ntok): a bin passes iff at most D' of the read's tokens
+// are missing from it, which is sum >= (L-q+1) - q*e.
+//
+// copies = 4 (the 256-bin tiles of q = 6): a tile row is 32 bytes, so the
+// row's bank group in shared memory is row & 3, and 16 reads of a warp
+// loading random rows collide in bank groups.  The order is then made
+// class-cyclic -- position p holds a token of row class p & 3, each class
+// rarest first, for as long as every class has tokens left; the rest follow
+// rarest first -- and copy k rotates every 16-token block by k positions.  A
+// group g of the all-bins kernel reads copy g & 3, so at each load the
+// warp's 16 groups cover the four bank groups four times each.  Every block
+// holds the same tokens in every copy, so the per-block early exit and every
+// sum are unchanged.
 __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
     const char* __restrict__ reads, const uint64_t* __restrict__ offsets,
     const uint32_t* __restrict__ lens, const uint16_t* __restrict__ e, uint32_t n_reads, uint32_t q,
     uint32_t max_read_len, uint32_t r4, uint32_t ts, const uint32_t* __restrict__ presence,
     uint16_t* __restrict__ tokens, uint32_t* __restrict__ meta, Ctl* ctl, Live live,
-    uint32_t max_e, uint64_t max_bases) {
+    uint32_t max_e, uint64_t max_bases, uint32_t copies) {
   __shared__ unsigned long long s_key[kTokWarps][kMaxStride];
   __shared__ uint16_t s_row[kTokWarps][kMaxStride];
+  __shared__ uint16_t s_seq[kTokWarps][kMaxStride];
+  __shared__ uint8_t s_crank[kTokWarps][kMaxStride];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   if (r >= live_reads(ctl, live, n_reads)) return;  // whole warps: warp syncs stay uniform
   if (e[r] > max_e && lane == 0) atomicOr(&ctl->status, kStatusArg);
   const uint32_t L = lens[r];
   const uint64_t off = offsets[r];
-  uint16_t* out = tokens + r * ts;
+  uint16_t* out = tokens + r * copies * ts;
   bool bad = false;
   if (L < q) {
     if (lane == 0) atomicOr(&ctl->status, kStatusShort);
@@ -55,16 +68,18 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
       v = (v << 2) | (((u >> 1) ^ (u >> 2)) & 3u);  // A0 C1 G2 T3
     }
     const uint32_t row = clean ? v : rowInvalid(r4);
-    if (!presence) {  // no order wanted (candidate lists): positions as they are
+    if (!presence && copies == 1) {  // no order wanted (candidate lists): positions as they are
       out[j] = (uint16_t)row;
       continue;
     }
     s_row[warp][j] = (uint16_t)row;
-    const unsigned long long rare = clean ? (unsigned long long)presence[row] + 1 : 0ull;
+    s_seq[warp][j] = (uint16_t)row;  // the order without a presence table
+    const unsigned long long rare =
+        !presence ? 0ull : clean ? (unsigned long long)presence[row] + 1 : 0ull;
     s_key[warp][j] = (rare << 8) | j;
   }
   __syncwarp();
-  if (presence) {
+  if (presence && copies == 1) {
     // rank = number of smaller keys (keys are distinct: position breaks ties)
     for (uint32_t j = lane; j < ntok; j += 32) {
       const unsigned long long mine = s_key[warp][j];
@@ -72,8 +87,51 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
       for (uint32_t i = 0; i < ntok; ++i) rank += s_key[warp][i] < mine;
       out[rank] = s_row[warp][j];
     }
+  } else if (copies > 1) {
+    if (presence) {
+      // rank of each token within its row class, and the size of each class
+      uint32_t cnt = 0;  // 4 byte counters: tokens of class c counted by this lane
+      for (uint32_t j = lane; j < ntok; j += 32) {
+        const unsigned long long mine = s_key[warp][j];
+        const uint32_t c = s_row[warp][j] & 3u;
+        uint32_t rank = 0;
+        for (uint32_t i = 0; i < ntok; ++i)
+          rank += (s_row[warp][i] & 3u) == c && s_key[warp][i] < mine;
+        s_crank[warp][j] = (uint8_t)rank;
+        cnt += 1u << (8 * c);
+      }
+      cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+      const uint32_t m = min(min(cnt & 0xFFu, (cnt >> 8) & 0xFFu),
+                             min((cnt >> 16) & 0xFFu, cnt >> 24));  // complete cycles
+      __syncwarp();
+      // the first 4m positions cycle through the classes; the tokens left over
+      // follow, rarest first
+      for (uint32_t j = lane; j < ntok; j += 32) {
+        const uint32_t rc = s_crank[warp][j];
+        uint32_t pos;
+        if (rc < m) {
+          pos = 4u * rc + (s_row[warp][j] & 3u);
+        } else {
+          const unsigned long long mine = s_key[warp][j];
+          uint32_t rank = 0;
+          for (uint32_t i = 0; i < ntok; ++i) rank += s_crank[warp][i] >= m && s_key[warp][i] < mine;
+          pos = 4u * m + rank;
+        }
+        s_seq[warp][pos] = s_row[warp][j];
+      }
+    }
+    __syncwarp();
+    // copy k: every 16-token block rotated by k positions
+    for (uint32_t k = 0; k < copies; ++k) {
+      uint16_t* o = out + k * ts;
+      for (uint32_t p = lane; p < ts; p += 32) {
+        const uint32_t src = (p & ~15u) | ((p + k) & 15u);
+        o[p] = src < ntok ? s_seq[warp][src] : (uint16_t)rowPad(r4);
+      }
+    }
   }
-  for (uint32_t j = ntok + lane; j < ts; j += 32) out[j] = (uint16_t)rowPad(r4);
+  if (copies == 1)
+    for (uint32_t j = ntok + lane; j < ts; j += 32) out[j] = (uint16_t)rowPad(r4);
   if (lane == 0) {
     uint32_t d = q * (uint32_t)e[r];
     if (d > ntok) d = ntok;
@@ -141,13 +199,14 @@ void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t*
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
                      uint32_t* meta, Ctl* ctl, cudaStream_t st, Live live, uint32_t max_e,
                      uint64_t max_bases) {
+  const uint32_t copies = rv.copies;
   if (rv.n_reads == 0) return;
   const uint32_t threads = kTokWarps * 32;
   uint64_t grid = ((uint64_t)rv.n_reads * 32 + threads - 1) / threads;
   ProfScope ps("tokenise", st);
   k_tokenise<<<(unsigned)grid, threads, 0, st>>>(reads, offsets, lens, e, rv.n_reads, ix.q,
                                                  ix.max_read_len, ix.r4, rv.ts, ix.presence, tokens,
-                                                 meta, ctl, live, max_e, max_bases);
+                                                 meta, ctl, live, max_e, max_bases, copies);
 }
 
 void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
