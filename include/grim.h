@@ -53,6 +53,7 @@ extern "C" {
 #define GRIM_E_BUSY (-13)          /* grim_server_submit: the server's queue is full            */
 #define GRIM_E_IO (-14)            /* a file could not be opened, read or written               */
 #define GRIM_E_FORMAT (-15)        /* not an index file of this library, or damaged             */
+#define GRIM_E_CANCELLED (-16)     /* a server request was cancelled before it ran              */
 
 /* ---- table layouts (bit mask for grim_build) ----------------------------- */
 /* Token-major: row t holds token t's bit for every bin, contiguous
@@ -403,6 +404,7 @@ typedef struct {
   uint64_t submitted, completed, batches, batch_reads, reads_done, records;
   uint64_t overflow_splits; /* merged batches rerun one request at a time */
   uint64_t queued_requests, queued_reads;
+  uint64_t cancelled;       /* requests cancelled before they ran         */
 } grim_server_stats;
 
 /* Create the slots' plans and start the scheduler.  The index must outlive
@@ -430,8 +432,13 @@ int grim_server_wait(grim_server* s, uint64_t ticket, int64_t timeout_us);
  * error and is released. */
 int grim_server_take(grim_server* s, uint64_t ticket, uint32_t* out_read, uint32_t* out_bin,
                      uint8_t* out_count, uint64_t cap, grim_request_info* info);
+/* Cancel a request still in the queue: it completes at once with
+ * GRIM_E_CANCELLED (grim_server_take returns that and releases it).
+ * GRIM_E_NOT_READY: it is already on the device and will complete normally.
+ * GRIM_E_ARG: unknown ticket, or the request has completed. */
+int grim_server_cancel(grim_server* s, uint64_t ticket);
 int grim_server_stats_get(grim_server* s, grim_server_stats* out);
-/* Drop queued requests, let batches on the device finish, stop, release. */
+/* Cancel queued requests, let batches on the device finish, stop, release. */
 void grim_server_free(grim_server* s);
 
 /* ---- helpers of the mapper around the filter (§GRIM-Filter, Fig. 5) ----- */

@@ -210,6 +210,7 @@ const char* grim_strerror(int s) {
     case GRIM_E_BUSY: return "the server's queue is full";
     case GRIM_E_IO: return "file could not be opened, read or written";
     case GRIM_E_FORMAT: return "not an index file of this library, or damaged";
+    case GRIM_E_CANCELLED: return "request cancelled before it ran";
     default: return "unknown status";
   }
 }

@@ -488,6 +488,31 @@ int grim_server_take(grim_server* s, uint64_t ticket, uint32_t* out_read, uint32
   return GRIM_OK;
 }
 
+int grim_server_cancel(grim_server* s, uint64_t ticket) {
+  if (!s) return GRIM_E_ARG;
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end() || it->second->done) return GRIM_E_ARG;
+  Request* r = it->second.get();
+  auto q = std::find(s->queue.begin(), s->queue.end(), r);
+  if (q == s->queue.end()) return GRIM_E_NOT_READY;  // on the device: it completes normally
+  s->queue.erase(q);
+  s->queued_reads -= r->n_reads;
+  r->status = GRIM_E_CANCELLED;
+  r->done = true;
+  r->info.status = GRIM_E_CANCELLED;
+  r->info.t_done_ns = now_ns();
+  r->reads = {};
+  r->offsets = {};
+  r->lens = {};
+  r->e = {};
+  r->cand = {};
+  r->cand_off = {};
+  s->st.cancelled++;
+  s->cv_done.notify_all();
+  return GRIM_OK;
+}
+
 int grim_server_stats_get(grim_server* s, grim_server_stats* out) {
   if (!s || !out) return GRIM_E_ARG;
   std::lock_guard<std::mutex> g(s->mu);
@@ -504,7 +529,7 @@ void grim_server_free(grim_server* s) {
     // then the scheduler returns
     std::lock_guard<std::mutex> g(s->mu);
     for (Request* r : s->queue) {
-      r->status = GRIM_E_ARG;
+      r->status = GRIM_E_CANCELLED;
       r->done = true;
     }
     s->queue.clear();

@@ -31,6 +31,7 @@ GRIM_E_NOT_READY = -12
 GRIM_E_BUSY = -13
 GRIM_E_IO = -14
 GRIM_E_FORMAT = -15
+GRIM_E_CANCELLED = -16
 GRIM_LOAD_VERIFY = 1
 GRIM_PLAN_CANDIDATES = 1
 GRIM_PLAN_HOST_IO = 2
@@ -51,7 +52,7 @@ EXPORTS = (
     "grim_plan_wait", "grim_plan_device_bytes", "grim_plan_free", "grim_default_coarse_factor",
     "grim_server_create", "grim_server_submit", "grim_server_wait", "grim_server_take",
     "grim_server_stats_get", "grim_server_free", "grim_save", "grim_load",
-    "grim_reverse_complement",
+    "grim_reverse_complement", "grim_server_cancel",
 )
 
 
@@ -114,7 +115,8 @@ class _RequestInfo(C.Structure):
 class _ServerStats(C.Structure):
     _fields_ = [("slots", C.c_uint32), ("reserved", C.c_uint32), ("device_bytes", C.c_uint64)] + [
         (n, C.c_uint64) for n in ("submitted", "completed", "batches", "batch_reads", "reads_done",
-                                  "records", "overflow_splits", "queued_requests", "queued_reads")]
+                                  "records", "overflow_splits", "queued_requests", "queued_reads",
+                                  "cancelled")]
 
 
 class _KTime(C.Structure):
@@ -195,6 +197,8 @@ def _lib() -> C.CDLL:
         lib.grim_server_wait.argtypes = [vp, u64, C.c_int64]
         lib.grim_server_take.restype = i32
         lib.grim_server_take.argtypes = [vp, u64, vp, vp, vp, u64, C.POINTER(_RequestInfo)]
+        lib.grim_server_cancel.restype = i32
+        lib.grim_server_cancel.argtypes = [vp, u64]
         lib.grim_server_stats_get.restype = i32
         lib.grim_server_stats_get.argtypes = [vp, C.POINTER(_ServerStats)]
         lib.grim_server_free.restype = None
@@ -877,6 +881,9 @@ class GrimServer:
         grim_server_wait(self, ticket, timeout_s)
         return grim_server_take(self, ticket)
 
+    def cancel(self, ticket: int) -> bool:
+        return grim_server_cancel(self, ticket)
+
     def stats(self) -> dict:
         return grim_server_stats_get(self)
 
@@ -949,6 +956,17 @@ def grim_server_take(server: GrimServer, ticket: int):
     if o_r is None:
         o_r, o_b, o_c = np.empty(0, np.uint32), np.empty(0, np.uint32), np.empty(0, np.uint8)
     return (o_r[:n], o_b[:n], o_c[:n]), ri
+
+
+def grim_server_cancel(server: GrimServer, ticket: int) -> bool:
+    """Cancel a queued request; False if it is already running (it then
+    completes normally)."""
+    rc = _lib().grim_server_cancel(server.handle, ticket)
+    if rc == GRIM_E_NOT_READY:
+        return False
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_server_cancel")
+    return True
 
 
 def grim_server_stats_get(server: GrimServer) -> dict:

@@ -232,3 +232,31 @@ def test_server_memory_budget_and_backpressure(world):
         got, _ = srv.result(t, timeout_s=60)
         assert_same(got, want)
     srv.close()
+
+
+def test_server_cancel(world):
+    """A queued request can be cancelled (it completes with GRIM_E_CANCELLED
+    and never runs); one already on the device completes normally; the
+    others are unaffected."""
+    from paper_1708_04329_gb300 import grim
+
+    g, oix, idx = world
+    # one slot of 25 reads: each 20-read request is a batch of its own, so
+    # the last of 40 requests waits behind the other 39
+    srv = grim.grim_server_create(idx, slots=1, max_reads=25, max_bases=25 * 250, max_e=12,
+                                  cap=20_000)
+    reqs = _requests(g, [20] * 40, 950)
+    ts = [srv.submit(**_host_args(rs)) for rs in reqs]
+    assert srv.cancel(ts[-1]) is True
+    with pytest.raises(grim.GrimError) as ei:
+        srv.result(ts[-1], timeout_s=60)
+    assert ei.value.code == grim.GRIM_E_CANCELLED
+    for t, rs in list(zip(ts, reqs))[:-1]:
+        got, _ = srv.result(t, timeout_s=60)
+        assert_same(got, oracle.filter(oix, rs))
+    with pytest.raises(grim.GrimError) as ei:
+        srv.cancel(ts[0])  # completed and taken
+    assert ei.value.code == grim.GRIM_E_ARG
+    st = srv.stats()
+    assert st["cancelled"] == 1 and st["completed"] == 39
+    srv.close()
