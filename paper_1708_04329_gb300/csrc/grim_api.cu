@@ -133,6 +133,7 @@ int index_alloc(uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len, uin
   }
   v.tm = ix->tm;
   v.bm = ix->bm;
+  v.bm_rows = bm_bins;
   v.presence = ix->presence;
   ix->v = v;
   cv.tm = ix->ctm;
@@ -261,17 +262,35 @@ int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_
   cudaMemsetAsync(codes + 2 * n32, 0, 2 * sizeof(uint32_t), st);
   cudaMemsetAsync(invalid + n32, 0xFF, 2 * sizeof(uint32_t), st);
   launch_pack_ref(ref, len, codes, invalid, st);
-  if (ix->tm) launch_build_token_major(codes, invalid, v, ix->tm, st);
-  if (ix->ctm) launch_build_token_major(codes, invalid, cv, ix->ctm, st);
+  // q >= 5: the token-major tables are bit transposes of the bin-major one
+  // (a scratch copy when the index keeps no bin-major table)
+  const bool transpose = v.q >= 5 && (ix->tm || ix->ctm);
+  uint32_t* bm = ix->bm;
+  if (!bm && transpose) {
+    e = cudaMallocAsync(&bm, bm_bins * v.wpb * sizeof(uint32_t), st);
+    if (e != cudaSuccess) {
+      cudaFreeAsync(codes, st);
+      cudaFreeAsync(invalid, st);
+      return fail(cuda_fail(e));
+    }
+  }
+  if (bm) {
+    if (bm_bins > v.num_bins)
+      cudaMemsetAsync(bm + v.num_bins * v.wpb, 0, (bm_bins - v.num_bins) * v.wpb * sizeof(uint32_t),
+                      st);
+    launch_build_bin_major(codes, invalid, v, bm, st);
+  }
+  if (transpose) {
+    if (ix->tm) launch_tm_from_bm(bm, v, v.wpb, 1, ix->tm, st);
+    if (ix->ctm) launch_tm_from_bm(bm, cv, v.wpb, f, ix->ctm, st);
+  } else {
+    if (ix->tm) launch_build_token_major(codes, invalid, v, ix->tm, st);
+    if (ix->ctm) launch_build_token_major(codes, invalid, cv, ix->ctm, st);
+  }
+  if (bm != ix->bm) cudaFreeAsync(bm, st);
   // token presence from the table the all-bins filter sweeps first
   if (ix->ctm) launch_row_popcount(ix->ctm, cv.r4, cv.wpad, ix->presence, st);
   else if (ix->tm) launch_row_popcount(ix->tm, v.r4, v.wpad, ix->presence, st);
-  if (ix->bm) {
-    if (bm_bins > v.num_bins)
-      cudaMemsetAsync(ix->bm + v.num_bins * v.wpb, 0,
-                      (bm_bins - v.num_bins) * v.wpb * sizeof(uint32_t), st);
-    launch_build_bin_major(codes, invalid, v, ix->bm, st);
-  }
   cudaFreeAsync(codes, st);
   cudaFreeAsync(invalid, st);
   e = cudaGetLastError();
@@ -398,7 +417,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
 
   CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
   launch_tokenise(reads, offsets, lens, e, v, rv, tokens, meta, ctl, st);
-  if (cand_mode) launch_check_candidates(cand, cand_off, n_reads, n_cand, v.num_bins, ctl, st);
+  if (cand_mode) launch_check_candidates(cand_off, n_reads, n_cand, ctl, st);
   CK(cudaGetLastError());
   // input errors end the call before the filter runs; the batch's largest
   // miss budget sizes the all-bins kernel's counters
@@ -418,7 +437,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   bool list_mode = cand_mode;
 
   if (cand_mode) {
-    launch_candidates(v, rv, cand, cand_off, ra, ctl, st);
+    launch_candidates(v, rv, cand, cand_off, ra, ctl, st, "candidates", {false, 0}, 0, true);
   } else {
     // all bins: coarse-then-exact when the index allows it and every read
     // needs enough of its tokens present for super-bins to fail early;

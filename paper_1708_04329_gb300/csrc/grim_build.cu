@@ -2,10 +2,11 @@
 // bit vector is set from the tokens that occur in it; Fig. 2):
 //   k_pack_ref          ASCII -> 2-bit codes + not-a-base mask
 //   k_build_bin_major   one warp per bin, bit vector in shared memory
-//   k_build_token_major one CTA per 1024-bin tile (256 bins at q = 6), the
-//                       tile's [4^q rows x tile words] bitmap in shared memory
-// Both table builders scan the packed reference directly; neither is a
-// transpose of the other.
+//   k_build_token_major one CTA per 1024-bin tile, the tile's [4^q rows x tile
+//                       words] bitmap in shared memory (q <= 4)
+//   k_tm_from_bm        q = 5, 6: token-major (and coarse token-major) tiles
+//                       as bit transposes of the bin-major vectors, ORed over
+//                       the members of each super-bin for the coarse table
 #include "grim_internal.cuh"
 
 namespace grim {
@@ -132,6 +133,71 @@ __global__ void __launch_bounds__(512) k_build_token_major(const uint32_t* __res
   }
 }
 
+template <int J>
+__device__ __forceinline__ void transpose_round(uint32_t (&x)[32], uint32_t m) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if ((k & J) == 0) {
+      const uint32_t t = ((x[k] >> J) ^ x[k + J]) & m;
+      x[k + J] ^= t;
+      x[k] ^= t << J;
+    }
+  }
+}
+
+// In-register transpose of a 32x32 bit matrix: on entry bit j of x[k] is
+// element (k, j); on exit bit k of x[j] is.  Five rounds swap the
+// off-diagonal halves of ever smaller diagonal blocks.
+__device__ __forceinline__ void transpose32(uint32_t (&x)[32]) {
+  transpose_round<16>(x, 0x0000FFFFu);
+  transpose_round<8>(x, 0x00FF00FFu);
+  transpose_round<4>(x, 0x0F0F0F0Fu);
+  transpose_round<2>(x, 0x33333333u);
+  transpose_round<1>(x, 0x55555555u);
+}
+
+// Token-major tile from the bin-major table (q >= 5, so a bin vector is a
+// whole number of 32-word chunks).  One CTA of 32 warps per tile of TW*32
+// (super-)bins; warp u takes bin group g = u % TW (32 bins) and token chunk
+// c = u / TW (1024 tokens).  Lane l loads word 32c + l of each of the
+// group's 32 vectors -- for a super-bin the OR of its f member bins, which
+// is exactly the super-bin's vector (its window is the union of theirs) --
+// transposes the 32x32 bits in registers, and leaves token rows in shared
+// memory (row t at t*TW + (t >> 5): one padding word per 32 rows keeps the
+// lanes' stores in distinct banks); the CTA then writes each token row's TW
+// words to the token-major table.
+template <int TW>
+__global__ void __launch_bounds__(1024) k_tm_from_bm(const uint32_t* __restrict__ bm,
+                                                     uint32_t wpb, uint32_t f, uint64_t units,
+                                                     uint32_t r4, uint64_t wpad,
+                                                     uint32_t* __restrict__ tm) {
+  extern __shared__ uint32_t s_rows[];
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t g = warp % TW, c = warp / TW;
+  const uint64_t u0 = (uint64_t)blockIdx.x * TW * 32 + g * 32;  // first unit of the group
+  uint32_t x[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const uint64_t u = u0 + k;
+    uint32_t w = 0;
+    if (u < units)
+      for (uint32_t m = 0; m < f; ++m) w |= __ldg(bm + (u * f + m) * wpb + c * 32 + lane);
+    x[k] = w;
+  }
+  transpose32(x);  // x[j]: token 32*(32c + lane) + j, bit k = unit u0 + k
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t t = 32u * (32u * c + lane) + j;
+    s_rows[t * TW + g + (t >> 5)] = x[j];
+  }
+  __syncthreads();
+  const uint64_t col0 = (uint64_t)blockIdx.x * TW;
+  for (uint32_t i = threadIdx.x; i < r4 * TW; i += blockDim.x) {
+    const uint32_t t = i / TW, col = i % TW;
+    tm[(uint64_t)t * wpad + col0 + col] = s_rows[t * TW + col + (t >> 5)];
+  }
+}
+
 // One CTA per token row: the number of set bits, i.e. how many (super-)bins
 // hold the token.
 __global__ void k_row_popcount(const uint32_t* __restrict__ tm, uint64_t words,
@@ -151,6 +217,25 @@ __global__ void k_row_popcount(const uint32_t* __restrict__ tm, uint64_t words,
 }
 
 }  // namespace
+
+void launch_tm_from_bm(const uint32_t* bm, const IndexView& unit_view, uint32_t wpb, uint32_t f,
+                       uint32_t* tm, cudaStream_t st) {
+  if (unit_view.num_bins == 0) return;
+  const uint32_t r4 = unit_view.r4;
+  const uint32_t tw = r4 <= 1024 ? 32u : 32768u / r4;  // tile words, as the filter's tiles
+  const size_t smem = ((size_t)r4 * tw + r4 / 32) * sizeof(uint32_t);
+  const uint64_t grid = unit_view.num_bins_pad / (tw * 32);
+  ProfScope ps("transpose_token_major", st);
+  if (tw == 32) {
+    cudaFuncSetAttribute(k_tm_from_bm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tm_from_bm<32><<<(unsigned)grid, 1024, smem, st>>>(bm, wpb, f, unit_view.num_bins, r4,
+                                                         unit_view.wpad, tm);
+  } else {
+    cudaFuncSetAttribute(k_tm_from_bm<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tm_from_bm<8><<<(unsigned)grid, 1024, smem, st>>>(bm, wpb, f, unit_view.num_bins, r4,
+                                                        unit_view.wpad, tm);
+  }
+}
 
 void launch_row_popcount(const uint32_t* tm, uint32_t rows, uint64_t words_per_row,
                          uint32_t* presence, cudaStream_t st) {

@@ -53,6 +53,7 @@ struct CandArgs {
   RecordsView rec;
   Ctl* ctl;
   Live live;
+  bool check_ids;  // caller's lists: an id outside [0, num_bins) is an error
 };
 
 constexpr int kWarps = 8;
@@ -213,6 +214,9 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_candidates(CandArgs a) {
   const uint64_t n_chunks = c_end > c_begin ? (c_end - c_begin + chunk - 1) / chunk : 0;
 
   uint32_t cur = 0xFFFFFFFFu, K = 0, thr = 0;  // the read whose planes are built
+  const bool check = a.check_ids;
+  const uint64_t last_row = a.ix.bm_rows - 1;
+  bool bad = false;  // this lane saw a candidate id outside [0, num_bins)
   uint32_t P[kRegPlanes][WL];
   // the next chunk is claimed one chunk ahead, so the atomic's latency
   // overlaps the current chunk's work
@@ -244,11 +248,16 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_candidates(CandArgs a) {
         for (uint64_t kb = pk; kb < c1; kb += (uint64_t)CPW * U) {
           uint32_t bn[U];
           load_ids<U, CPW>(a.cand, kb + (uint64_t)CPW * U, c1, slot, bn);
+          // the caller's ids are checked here, where they are read anyway: an
+          // id outside [0, num_bins) fails the call, never passes, and its
+          // gather is clamped inside the table
           uint32_t v[U][WL];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            if (kb + (uint64_t)u * CPW + slot < c1)
-              load_words<WL>(a.ix.bm + (uint64_t)bc[u] * WPB + sub * WL, v[u]);
+            const bool in = kb + (uint64_t)u * CPW + slot < c1;
+            bad |= check && in && bc[u] >= a.ix.num_bins;
+            const uint64_t row = min((uint64_t)bc[u], last_row);
+            if (in) load_words<WL>(a.ix.bm + row * WPB + sub * WL, v[u]);
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
@@ -284,6 +293,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_candidates(CandArgs a) {
       re = re_next;
     }
   }
+  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(&a.ctl->status, kStatusBadCand);
 }
 
 template <int WPB, int U>
@@ -312,10 +322,10 @@ void launch_t(const CandArgs& a, cudaStream_t st, const char* name, uint32_t unr
 
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
                        const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
-                       const char* prof_name, Live live, uint32_t unroll) {
+                       const char* prof_name, Live live, uint32_t unroll, bool check_ids) {
   if (unroll == 0) unroll = kDefaultCandUnroll;
   if (rv.n_reads == 0) return;
-  CandArgs a{ix, rv, cand, cand_off, rec, ctl, live};
+  CandArgs a{ix, rv, cand, cand_off, rec, ctl, live, check_ids};
   switch (ix.wpb) {
     case 1: launch_t<1>(a, st, prof_name, unroll); break;
     case 2: launch_t<2>(a, st, prof_name, unroll); break;

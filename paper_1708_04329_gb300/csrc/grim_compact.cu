@@ -51,41 +51,57 @@ __global__ void __launch_bounds__(kSortThreads) k_rs_hist(const unsigned long lo
 }
 
 // Exclusive scan, with one block, of the digit-major histogram of the live
-// blocks: entry (d, blk) at h[d * nb + blk] for blk < nb_live.  Thread t owns
-// a contiguous segment of the 256 * nb_live entries, scans its sums across
-// the block, then rewrites its segment.
-__device__ __forceinline__ uint64_t hist_at(uint64_t i, uint64_t nb_live, uint64_t nb) {
-  return (i / nb_live) * nb + (i % nb_live);
+// blocks: entry (d, blk) at h[d * nb + blk] for blk < nb_live, scanned in
+// the logical order i = d * nb_live + blk.  Warp w owns the logical range
+// [w*S, (w+1)*S): it sums the range (32 consecutive entries per step, so the
+// loads coalesce), the 32 warp totals are scanned, and each warp rescans its
+// range with shuffles, carrying its running offset.
+__device__ __forceinline__ uint64_t hist_at(uint32_t i, uint32_t nb_live, uint64_t nb) {
+  return (uint64_t)(i / nb_live) * nb + (i % nb_live);
 }
 
 __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ h, uint64_t nb, uint64_t n,
                                                   const unsigned long long* n_live, const Ctl* gc,
                                                   uint32_t gate) {
-  __shared__ uint32_t part[1024];
+  __shared__ uint32_t s_warp[32];
   if (gate_off(gc, gate)) return;
   n = live_n(n_live, n);
-  const uint64_t nb_live = (n + kSortTile - 1) / kSortTile;
+  const uint32_t nb_live = (uint32_t)((n + kSortTile - 1) / kSortTile);
   if (nb_live == 0) return;
-  const uint64_t m = 256 * nb_live;
-  const uint64_t per = (m + 1023) / 1024;
-  const uint64_t lo = threadIdx.x * per;
-  const uint64_t hi = lo + per < m ? lo + per : m;
-  uint32_t s = 0;
-  for (uint64_t i = lo; i < hi; ++i) s += h[hist_at(i, nb_live, nb)];
-  part[threadIdx.x] = s;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t m = 256u * nb_live;
+  const uint32_t span = (m + 31) / 32;
+  const uint32_t lo = min(warp * span, m), hi = min(lo + span, m);
+  uint32_t total = 0;
+  for (uint32_t i = lo + lane; i < hi; i += 32) total += h[hist_at(i, nb_live, nb)];
+  total = __reduce_add_sync(0xFFFFFFFFu, total);
+  if (lane == 0) s_warp[warp] = total;
   __syncthreads();
-  for (uint32_t d = 1; d < 1024; d <<= 1) {
-    const uint32_t v = threadIdx.x >= d ? part[threadIdx.x - d] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  if (warp == 0) {
+    const uint32_t v = s_warp[lane];
+    uint32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= (uint32_t)d) incl += t;
+    }
+    s_warp[lane] = incl - v;  // exclusive
   }
-  uint32_t run = part[threadIdx.x] - s;
-  for (uint64_t i = lo; i < hi; ++i) {
-    const uint64_t j = hist_at(i, nb_live, nb);
-    const uint32_t v = h[j];
-    h[j] = run;
-    run += v;
+  __syncthreads();
+  uint32_t carry = s_warp[warp];
+  for (uint32_t c = lo; c < hi; c += 32) {
+    const uint32_t i = c + lane;
+    const bool in = i < hi;
+    const uint64_t j = in ? hist_at(i, nb_live, nb) : 0;
+    const uint32_t v = in ? h[j] : 0u;
+    uint32_t incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+      if (lane >= (uint32_t)d) incl += t;
+    }
+    if (in) h[j] = carry + incl - v;
+    carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
   }
 }
 

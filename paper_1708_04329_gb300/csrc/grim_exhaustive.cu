@@ -44,7 +44,7 @@
 namespace grim {
 namespace {
 
-constexpr int kMaxThreads = 512;
+constexpr int kMaxThreads = 768;  // 24 warps: 80 registers a thread
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 
@@ -404,7 +404,7 @@ void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, cu
   const size_t tile_bytes = (size_t)(ix.r4 + 2) * kRowBytes;
   uint32_t threads = kMaxThreads;
   while (threads > 64 && tile_bytes + (size_t)(threads / GL) * a.slot_bytes + 32 > kSmemLimit)
-    threads /= 2;
+    threads -= 32;
   const size_t smem = tile_bytes + (size_t)(threads / GL) * a.slot_bytes + 32;
   // small batches on few tiles need fewer CTAs (graph launches size for the
   // largest batch and let surplus CTAs find no work)

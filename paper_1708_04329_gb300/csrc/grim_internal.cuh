@@ -74,6 +74,7 @@ __host__ __device__ inline uint32_t rowPad(uint32_t r4) { return r4 + 1; }
 
 struct IndexView {
   uint64_t n, num_bins, num_bins_pad, wpad;  // wpad = num_bins_pad / 32 words per row
+  uint64_t bm_rows;  // rows of the bin-major table: num_bins padded to whole super-bins
   uint32_t B, q, ext, max_read_len, r4, wpb;
   const uint32_t* tm;  // token-major [r4][wpad]
   const uint32_t* bm;  // bin-major [num_bins][wpb]
@@ -108,6 +109,10 @@ void launch_build_bin_major(const uint32_t* codes, const uint32_t* invalid, cons
                             uint32_t* bm, cudaStream_t st);
 void launch_build_token_major(const uint32_t* codes, const uint32_t* invalid, const IndexView& ix,
                               uint32_t* tm, cudaStream_t st);
+// Token-major table of `unit_view` (bins, or super-bins of f bins) from the
+// bin-major table bm [units * f][wpb]; q >= 5
+void launch_tm_from_bm(const uint32_t* bm, const IndexView& unit_view, uint32_t wpb, uint32_t f,
+                       uint32_t* tm, cudaStream_t st);
 // presence[t] = popcount of row t of a token-major table
 void launch_row_popcount(const uint32_t* tm, uint32_t rows, uint64_t words_per_row,
                          uint32_t* presence, cudaStream_t st);
@@ -122,9 +127,11 @@ void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t*
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
                      uint32_t* meta, Ctl* ctl, cudaStream_t st, Live live = {false, 0},
                      uint32_t max_e = 0xFFFFu, uint64_t max_bases = ~0ull);
-void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
-                             uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st,
-                             Live live = {false, 0});
+// CSR offsets of the caller's lists: non-decreasing, ending at n_cand
+// (kStatusBadCsr otherwise); the ids themselves are checked by the
+// candidate kernel
+void launch_check_candidates(const uint64_t* cand_off, uint32_t n_reads, uint64_t n_cand, Ctl* ctl,
+                             cudaStream_t st, Live live = {false, 0});
 
 // bins per tile of the all-bins kernel for a table of r4 = 4^q rows
 uint32_t exhaustive_tile_bins(uint32_t r4);
@@ -132,11 +139,15 @@ uint32_t exhaustive_tile_bins(uint32_t r4);
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st,
                        const char* prof_name = "exhaustive", Live live = {false, 0});
-// unroll: candidate gathers in flight per lane group (1, 2, 4 or 8; 0 = default)
+// unroll: candidate gathers in flight per lane group (1, 2, 4 or 8; 0 =
+// default).  check_ids: the lists are the caller's; an id outside
+// [0, num_bins) sets kStatusBadCand (and is not gathered).  Internal lists
+// (survivor members) may hold zero-padding bins past num_bins: they are
+// gathered and never pass.
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
                        const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
                        const char* prof_name = "candidates", Live live = {false, 0},
-                       uint32_t unroll = 0);
+                       uint32_t unroll = 0, bool check_ids = false);
 
 // Radix sort of n (key, count) records by the low key_bits bits of the key,
 // followed by the split into the caller's (read, bin, count) arrays.

@@ -154,10 +154,9 @@ int capture(grim_plan* p) {
                   reinterpret_cast<uint16_t*>(ws + L.tok), reinterpret_cast<uint32_t*>(ws + L.meta),
                   p->ctl, st, live, d.max_e, d.max_bases);
   if (p->cand_mode) {
-    launch_check_candidates(B.cand, B.cand_off, d.max_reads, d.max_cand, v.num_bins,
-                            p->ctl, st, live);
+    launch_check_candidates(B.cand_off, d.max_reads, d.max_cand, p->ctl, st, live);
     launch_candidates(v, rv, B.cand, B.cand_off, ra, p->ctl, st, "candidates", live,
-                      d.cand_unroll);
+                      d.cand_unroll, true);
     k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlFinal, 0, 0, 0);
     sort_and_emit(ra, rb, d.cap, bit_length(d.max_cand ? d.max_cand - 1 : 0), ws + L.hist, true,
                   bin_bits, B.cand, B.cand_off, d.max_reads, B.out_read,

@@ -1,6 +1,6 @@
 // Read tokenising (§GRIM-Filter step 1: every token of the read is
 // extracted) and the per-read threshold of Fig. 3, plus the validation of
-// candidate lists.
+// candidate-list offsets.
 #include "grim_internal.cuh"
 
 namespace grim {
@@ -144,21 +144,14 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
   }
 }
 
-__global__ void k_check_candidates(const int32_t* __restrict__ cand,
-                                   const uint64_t* __restrict__ cand_off, uint32_t n_reads,
-                                   uint64_t n_cand, uint64_t num_bins, Ctl* ctl, Live live) {
+__global__ void k_check_csr(const uint64_t* __restrict__ cand_off, uint32_t n_reads,
+                            uint64_t n_cand, Ctl* ctl, Live live) {
   const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (live.on) {
     n_reads = ctl->live_reads;
     n_cand = ctl->live_cand;
   }
-  if (i < n_cand) {
-    int32_t b = cand[i];
-    if (b < 0 || (uint64_t)b >= num_bins) atomicOr(&ctl->status, kStatusBadCand);
-  }
-  if (i < n_reads) {
-    if (cand_off[i] > cand_off[i + 1]) atomicOr(&ctl->status, kStatusBadCsr);
-  }
+  if (i < n_reads && cand_off[i] > cand_off[i + 1]) atomicOr(&ctl->status, kStatusBadCsr);
   if (i == 0 && cand_off[n_reads] != n_cand) atomicOr(&ctl->status, kStatusBadCsr);
 }
 
@@ -209,14 +202,11 @@ void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t*
                                                  meta, ctl, live, max_e, max_bases, copies);
 }
 
-void launch_check_candidates(const int32_t* cand, const uint64_t* cand_off, uint32_t n_reads,
-                             uint64_t n_cand, uint64_t num_bins, Ctl* ctl, cudaStream_t st,
-                             Live live) {
-  uint64_t n = n_cand > n_reads ? n_cand : n_reads;
-  if (n == 0) n = 1;
+void launch_check_candidates(const uint64_t* cand_off, uint32_t n_reads, uint64_t n_cand, Ctl* ctl,
+                             cudaStream_t st, Live live) {
+  const uint64_t n = (uint64_t)n_reads + 1;
   ProfScope ps("check_candidates", st);
-  k_check_candidates<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand, cand_off, n_reads, n_cand,
-                                                                  num_bins, ctl, live);
+  k_check_csr<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cand_off, n_reads, n_cand, ctl, live);
 }
 
 }  // namespace grim
