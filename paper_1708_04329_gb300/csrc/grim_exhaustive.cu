@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
     // per-group state (identical in the group's 8 lanes); the group's slot
     // holds two token rows: `buf` is the current read's, buf^1 the next's
     uint32_t cur = kNone, nxt = kNone, nxt_meta = 0, buf = 1;
-    uint32_t blk = 0, nblk = 0, ntok = 0, bias = 0, executed = 0;
+    uint32_t nblk = 0, ntok = 0, bias = 0, executed = 0;
     bool fin = false;
     Counters<P> c;
     c.init(0);
@@ -282,101 +282,109 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();  // tile staged
 
-    for (;;) {
-      // (1) groups without a read switch to the one whose tokens were copied
-      //     ahead, and start copying the read after it
-      const bool need = !fin && cur == kNone;
-      if (__any_sync(0xFFFFFFFFu, need)) {
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncwarp();
-        if (need) {
-          if (nxt == kNone) {
-            fin = true;
-          } else {
-            cur = nxt;
-            buf ^= 1u;
-            ntok = nxt_meta & 0xFFu;
-            const uint32_t d = (nxt_meta >> 8) & 0xFFu;
-            bias = (1u << P) - (d + 1u);
-            nblk = (ntok + kBlockTokens - 1) / kBlockTokens;
-            blk = 0;
-            c.init(bias);
-          }
+    // (1) groups without a read switch to the one whose tokens were copied
+    //     ahead, and start copying the read after it; `tp` is the shared
+    //     address of a group's next 16-token block, `left` its blocks left
+    //     (finished groups apply padding tokens, their results ignored)
+    uint32_t tp = pad_tokens, step = 0, left = 0;
+    auto switch_reads = [&](bool need) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncwarp();
+      if (need) {
+        if (nxt == kNone) {
+          fin = true;
+        } else {
+          cur = nxt;
+          buf ^= 1u;
+          ntok = nxt_meta & 0xFFu;
+          const uint32_t d = (nxt_meta >> 8) & 0xFFu;
+          bias = (1u << P) - (d + 1u);
+          nblk = (ntok + kBlockTokens - 1) / kBlockTokens;
+          c.init(bias);
         }
-        const bool take = need && !fin;
-        uint32_t k = 0;
-        if (take && li == 0) k = atomicAdd(&s_next, 1u);
-        k = __shfl_sync(0xFFFFFFFFu, k, grp * GL);
-        if (take) {
-          nxt = k < nr ? r0 + k : kNone;
-          if (nxt != kNone) {
-            nxt_meta = __ldg(a.rv.meta + nxt);
-            const char* src = reinterpret_cast<const char*>(
-                a.rv.tokens + ((uint64_t)nxt * a.rv.copies + copy) * a.rv.ts);
-            const uint32_t dst = slot + (buf ^ 1u) * a.row_stride;
-            for (uint32_t ch = li; ch < row_chunks; ch += GL)
-              asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst + ch * 16u),
-                           "l"(src + ch * 16u));
-          }
-        }
-        asm volatile("cp.async.commit_group;");
+        tp = fin ? pad_tokens : slot + buf * a.row_stride;
+        step = fin ? 0u : 32u;
+        left = fin ? ~0u : nblk;
       }
-      if (__all_sync(0xFFFFFFFFu, fin)) break;
+      const bool take = need && !fin;
+      uint32_t k = 0;
+      if (take && li == 0) k = atomicAdd(&s_next, 1u);
+      k = __shfl_sync(0xFFFFFFFFu, k, grp * GL);
+      if (take) {
+        nxt = k < nr ? r0 + k : kNone;
+        if (nxt != kNone) {
+          nxt_meta = __ldg(a.rv.meta + nxt);
+          const char* src = reinterpret_cast<const char*>(
+              a.rv.tokens + ((uint64_t)nxt * a.rv.copies + copy) * a.rv.ts);
+          const uint32_t dst = slot + (buf ^ 1u) * a.row_stride;
+          for (uint32_t ch = li; ch < row_chunks; ch += GL)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst + ch * 16u),
+                         "l"(src + ch * 16u));
+        }
+      }
+      asm volatile("cp.async.commit_group;");
+    };
+    switch_reads(true);
+    const uint32_t gmask = kGroupMask << (grp * GL);
+    bool active = __any_sync(0xFFFFFFFFu, !fin);
 
-      // (2) one 16-token block for all four groups (finished groups apply
-      //     padding tokens; their results are ignored)
+    while (active) {
+      // (2) one 16-token block for all four groups
       {
-        const uint32_t tp = fin ? pad_tokens : slot + buf * a.row_stride + blk * 32u;
         const uint4 t0 = lds128(tp), t1 = lds128(tp + 16u);
         const uint32_t tw[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
         add_block<P>(c, tw, lane_base, a);
       }
-      if (!fin) {
-        ++blk;
-        ++executed;
-      }
+      tp += step;
+      --left;
 
-      // (3) a read ends when every bin of its tile is dead or its tokens are used up
+      // (3) a read ends when every bin of its tile is dead or its tokens are
+      //     used up; one ballot per block, the rest only when some group ends
       const uint32_t all_dead = c.dead[0] & c.dead[1] & c.dead[2] & c.dead[3];
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, all_dead == ~0u);
-      const bool gdead = ((bal >> (grp * GL)) & kGroupMask) == kGroupMask;
-      const bool done = !fin && (gdead || blk >= nblk);
-      const bool emit = done && !gdead;
-      if (__any_sync(0xFFFFFFFFu, emit)) {
-        uint32_t pm[4], cnt = 0;
+      const bool gdead = (bal & gmask) == gmask;
+      const bool done = !fin && (gdead || left == 0);
+      if (__any_sync(0xFFFFFFFFu, done)) {
+        if (done) executed += nblk - left;
+        const bool emit = done && !gdead;
+        if (__any_sync(0xFFFFFFFFu, emit)) {
+          uint32_t pm[4], cnt = 0;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          pm[w] = emit ? (~c.dead[w] & vmask[w]) : 0u;
-          cnt += __popc(pm[w]);
-        }
-        uint32_t incl = cnt;
+          for (int w = 0; w < 4; ++w) {
+            pm[w] = emit ? (~c.dead[w] & vmask[w]) : 0u;
+            cnt += __popc(pm[w]);
+          }
+          uint32_t incl = cnt;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-          if (lane >= (uint32_t)d) incl += t;
-        }
-        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        unsigned long long base = 0;
-        if (lane == 0 && tot) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)tot);
-        base = __shfl_sync(0xFFFFFFFFu, base, 0);
-        unsigned long long pos = base + incl - cnt;
+          for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= (uint32_t)d) incl += t;
+          }
+          const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+          unsigned long long base = 0;
+          if (lane == 0 && tot) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)tot);
+          base = __shfl_sync(0xFFFFFFFFu, base, 0);
+          unsigned long long pos = base + incl - cnt;
 #pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          uint32_t m = pm[w];
-          while (m) {
-            const uint32_t bit = __ffs(m) - 1;
-            m &= m - 1;
-            const uint32_t misses = c.value(w, bit) - bias;
-            const uint64_t bin = (uint64_t)tile * kTileBinsT + (li * 4u + w) * 32u + bit;
-            if (pos < a.rec.cap) {
-              a.rec.keys[pos] = ((unsigned long long)cur << a.bin_bits) | bin;
-              a.rec.counts[pos] = (uint8_t)(ntok - misses);
+          for (int w = 0; w < 4; ++w) {
+            uint32_t m = pm[w];
+            while (m) {
+              const uint32_t bit = __ffs(m) - 1;
+              m &= m - 1;
+              const uint32_t misses = c.value(w, bit) - bias;
+              const uint64_t bin = (uint64_t)tile * kTileBinsT + (li * 4u + w) * 32u + bit;
+              if (pos < a.rec.cap) {
+                a.rec.keys[pos] = ((unsigned long long)cur << a.bin_bits) | bin;
+                a.rec.counts[pos] = (uint8_t)(ntok - misses);
+              }
+              ++pos;
             }
-            ++pos;
           }
         }
+        if (done) cur = kNone;
+        switch_reads(done);
+        active = __any_sync(0xFFFFFFFFu, !fin);
       }
-      if (done) cur = kNone;
     }
     // one count per group (its lanes agree), one atomic per warp and item
     uint32_t ex = li == 0 ? executed : 0u;
