@@ -11,6 +11,11 @@ One step = one pass of the whole hot path over one batch of synthetic input:
 ``e2e`` is the same through grim_build_host / grim_filter_host with pinned
 host buffers, the host<->device copies inside the timed region.
 
+``serving`` (single-GPU runs) adds a short serving measurement: the same
+genome's table resident, Poisson arrivals of read batches served with
+continuous batching, latency percentiles at 0.85 of the measured capacity
+(``--workload serve`` runs the full sweep and a 60 s trace).
+
 ``--impl reference`` times the CPU oracle (the only reference there is: the
 paper publishes no code) on a bounded sample of the same workload.
 
@@ -68,6 +73,8 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-serve", action="store_true",
+                   help="skip the short serving measurement of the headline line")
     p.add_argument("--traffic", type=float, default=None,
                    help="DRAM bytes of one launch of the dominant kernel, from an ncu capture")
     return p.parse_args()
@@ -345,6 +352,8 @@ def run_native(args, rank, world, local):
         line["e2e"] = run_e2e(args, w, st)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if rank == 0 and world == 1 and not args.no_serve:
+        line["serving"] = serving_leg(w["genome"])
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -687,6 +696,46 @@ def _plain_trace(idx, rs, trace, paced: bool, time_limit_s: float) -> dict:
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
             "p999_ms": float(np.percentile(lat_ms, 99.9)), "max_ms": float(lat_ms.max()),
             "completed_trace": len(lat) == len(trace["t"])}
+
+
+def serving_leg(g, trace_s: float = 10.0, load: float = 0.85) -> dict:
+    """A short serving measurement for the headline line: the same genome's
+    table (built for reads up to 250 bp) resident, the serving workload's
+    requests, capacity with the queue kept full, then a Poisson trace at
+    `load` of that capacity; latency percentiles of that trace."""
+    import torch
+
+    from paper_1708_04329_gb300 import grim, synth
+
+    w = synth.serving(pool_reads=500_000, g=g)
+    rs = w["reads"]
+    ref = torch.from_numpy(g).cuda()
+    idx = grim.grim_build(ref, w["B"], w["q"], w["max_read_len"], grim.GRIM_LAYOUT_ALL)
+    del ref
+    torch.cuda.synchronize()
+    slot_reads = 16384
+    try:
+        with grim.grim_server_create(idx, slots=3, max_reads=slot_reads,
+                                     max_bases=slot_reads * 250, max_e=int(rs.e.max()),
+                                     cap=32 * slot_reads, mem_budget=8 << 30) as srv:
+            _serve_trace(srv, rs, synth.request_trace(1.0, 100.0, rs.n, seed=60), paced=False,
+                         time_limit_s=1.0)
+            cap_run = _serve_trace(srv, rs, synth.request_trace(100.0, 1000.0, rs.n, seed=61),
+                                   paced=False, time_limit_s=3.0)
+            capacity = cap_run["requests"] / cap_run["elapsed_s"]
+            rate = load * capacity
+            main = _serve_trace(srv, rs, synth.request_trace(trace_s, rate, rs.n, seed=63),
+                                paced=True)
+    finally:
+        idx.close()
+    return {"value": round(main["reads_per_s"], 1), "unit": UNIT,
+            "offered_batches_per_s": round(rate, 1), "load": load,
+            "latency_ms": {k: round(main[k + "_ms"], 2) for k in ("p50", "p99", "p999")},
+            "capacity_reads_per_s": round(cap_run["reads_per_s"], 1),
+            "mean_requests_per_batch": round(main["mean_requests_per_batch"], 2),
+            "trace": (f"{trace_s:.0f} s Poisson trace, {main['requests']} requests, sizes "
+                      "log-uniform 1..8192, L in {100,150,250}, e <= 0.05 L; 3 slots; "
+                      "bench.py --workload serve runs the full 60 s measurement")}
 
 
 def run_serve(args, rank, world, local):

@@ -438,7 +438,8 @@ int grim_server_take(grim_server* s, uint64_t ticket, uint32_t* out_read, uint32
  * GRIM_E_ARG: unknown ticket, or the request has completed. */
 int grim_server_cancel(grim_server* s, uint64_t ticket);
 int grim_server_stats_get(grim_server* s, grim_server_stats* out);
-/* Cancel queued requests, let batches on the device finish, stop, release. */
+/* Cancel queued requests, let batches on the device finish, stop, release.
+ * No other call on the server may be running or follow. */
 void grim_server_free(grim_server* s);
 
 /* ---- helpers of the mapper around the filter (§GRIM-Filter, Fig. 5) ----- */

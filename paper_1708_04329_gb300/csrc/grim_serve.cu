@@ -234,7 +234,17 @@ struct grim_server {
     cv_done.notify_all();
   }
 
+  // the scheduler thread: any exception (an allocation failing while a
+  // result is copied) ends the server with GRIM_E_NOMEM rather than the process
   void run() {
+    try {
+      loop();
+    } catch (...) {
+      fail_all(GRIM_E_NOMEM);
+    }
+  }
+
+  void loop() {
     cudaSetDevice(device);
     uint32_t idle_spins = 0;
     for (;;) {
@@ -536,6 +546,7 @@ void grim_server_free(grim_server* s) {
     s->queued_reads = 0;
     s->stop = true;
   }
+  s->cv_done.notify_all();
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();
   destroy_slots(s);
