@@ -47,6 +47,7 @@ namespace {
 constexpr int kMaxThreads = 768;  // 24 warps: 80 registers a thread
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
+constexpr uint64_t kRangeTokenBytes = 48ull << 20;  // token rows of one read range: L2-resident
 
 #define LOP3(d, a, b, c, lut) \
   asm("lop3.b32 %0, %1, %2, %3, " #lut ";" : "=r"(d) : "r"(a), "r"(b), "r"(c))
@@ -192,12 +193,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
   // persistent grid, each range at least 64 reads
   const uint32_t n_reads = live_reads(a.ctl, a.live, a.rv.n_reads);
   if (n_reads == 0) return;
+  // enough ranges to balance the persistent grid when tiles are few, and
+  // ranges whose token rows fit in L2 when there are many reads: items are
+  // then taken range by range, so the CTAs sweeping different tiles at the
+  // same time share one range's token rows in L2 instead of each streaming
+  // every read's tokens from DRAM
   uint32_t n_ranges = (4u * a.sms + a.n_tiles - 1) / a.n_tiles;
+  const uint64_t token_bytes = (uint64_t)n_reads * a.rv.ts * 2u * a.rv.copies;
+  const uint32_t l2_ranges = (uint32_t)((token_bytes + kRangeTokenBytes - 1) / kRangeTokenBytes);
+  n_ranges = max(n_ranges, l2_ranges);
   n_ranges = min(n_ranges, (n_reads + 63) / 64);
   n_ranges = max(n_ranges, 1u);
   const uint32_t per = (n_reads + n_ranges - 1) / n_ranges;
   n_ranges = (n_reads + per - 1) / per;
   const uint32_t n_items = a.n_tiles * n_ranges;
+  const bool range_major = a.n_tiles >= 4u * a.sms;
 
   uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem);
   const uint32_t tile_bytes = (r4 + 2) * kRowBytes;
@@ -228,7 +238,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= n_items) break;
-    const uint32_t tile = item / n_ranges, range = item % n_ranges;
+    const uint32_t tile = range_major ? item % a.n_tiles : item / n_ranges;
+    const uint32_t range = range_major ? item / a.n_tiles : item % n_ranges;
     const uint32_t r0 = range * per;
     const uint32_t nr = min(per, n_reads - r0);
 
