@@ -48,6 +48,7 @@ constexpr int kMaxThreads = 768;  // 24 warps: 80 registers a thread
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 constexpr uint64_t kRangeTokenBytes = 48ull << 20;  // token rows of one read range: L2-resident
+constexpr uint32_t kSlotBlocksNarrow = 7;           // slot blocks per read, 256-bin tiles
 
 #define LOP3(d, a, b, c, lut) \
   asm("lop3.b32 %0, %1, %2, %3, " #lut ";" : "=r"(d) : "r"(a), "r"(b), "r"(c))
@@ -120,8 +121,9 @@ struct ExhArgs {
   uint32_t bin_bits;
   uint32_t n_tiles, sms;
   Live live;
-  uint32_t row_stride;  // bytes of one token row in a group slot (multiple of 16)
+  uint32_t row_stride;  // bytes of one token row in a group slot (multiple of 32)
   uint32_t slot_bytes;  // bytes of a group slot: two token rows
+  uint32_t slot_blocks; // 16-token blocks a slot row holds; later blocks come from L2
   uint32_t c_row, c_hi, c_lo;  // TW*4, 65536, -65536: multipliers of the address math
   Ctl* ctl;
 };
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
   // the token copy this group reads (block-rotated copies spread the groups'
   // 32-byte rows over the bank groups at q = 6)
   const uint32_t copy = a.rv.copies > 1 ? grp % a.rv.copies : 0u;
-  const uint32_t row_chunks = a.rv.ts * 2u / 16u;  // 16-byte chunks of a token row
+  const uint32_t row_chunks = a.row_stride / 16u;  // 16-byte chunks of a slot row
 
   for (;;) {
     asm volatile("cp.async.wait_all;" ::: "memory");
@@ -340,9 +342,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
     bool active = __any_sync(0xFFFFFFFFu, !fin);
 
     while (active) {
-      // (2) one 16-token block for all four groups
+      // (2) one 16-token block for all groups: from the slot, or for the
+      //     blocks past the slot's rows (long reads at q = 6) from L2
       {
-        const uint4 t0 = lds128(tp), t1 = lds128(tp + 16u);
+        uint4 t0, t1;
+        const uint32_t bi = nblk - left;  // this read's block index
+        if (TW == 32 || fin || bi < a.slot_blocks) {  // 1024-bin tiles: whole reads in slots
+          t0 = lds128(tp);
+          t1 = lds128(tp + 16u);
+        } else {
+          const uint4* g = reinterpret_cast<const uint4*>(
+              a.rv.tokens + ((uint64_t)cur * a.rv.copies + copy) * a.rv.ts + bi * kBlockTokens);
+          t0 = __ldg(g);
+          t1 = __ldg(g + 1);
+        }
         const uint32_t tw[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
         add_block<P>(c, tw, lane_base, a);
       }
@@ -458,7 +471,13 @@ void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec
   a.rec = rec;
   a.bin_bits = bin_bits;
   a.live = live;
-  a.row_stride = rv.ts * 2u;
+  // a slot row holds a read's first blocks: all of them for the 1024-bin
+  // tiles; at most kSlotBlocksNarrow for the 256-bin tiles of q = 6, whose
+  // 128 KB tile leaves little room for the sixteen groups' slots of a warp
+  // (reads that survive longer fetch their later blocks from L2)
+  const uint32_t blocks = rv.ts / kBlockTokens;
+  a.slot_blocks = ix.r4 <= 1024 ? blocks : min(blocks, kSlotBlocksNarrow);
+  a.row_stride = a.slot_blocks * kBlockTokens * 2u;
   // slots of consecutive groups start 32 bytes apart modulo 128, so the
   // groups of a warp mostly read their tokens from different banks
   a.slot_bytes = (2u * a.row_stride + 127u) / 128u * 128u + 32u;
