@@ -48,7 +48,7 @@ constexpr int kMaxThreads = 768;  // 24 warps: 80 registers a thread
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 constexpr uint64_t kRangeTokenBytes = 48ull << 20;  // token rows of one read range: L2-resident
-constexpr uint32_t kSlotBlocksNarrow = 7;           // slot blocks per read, 256-bin tiles
+constexpr uint32_t kSlotBlocksNarrow = 1;           // slot blocks per read, 256-bin tiles
 
 #define LOP3(d, a, b, c, lut) \
   asm("lop3.b32 %0, %1, %2, %3, " #lut ";" : "=r"(d) : "r"(a), "r"(b), "r"(c))
@@ -472,9 +472,10 @@ void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec
   a.bin_bits = bin_bits;
   a.live = live;
   // a slot row holds a read's first blocks: all of them for the 1024-bin
-  // tiles; at most kSlotBlocksNarrow for the 256-bin tiles of q = 6, whose
-  // 128 KB tile leaves little room for the sixteen groups' slots of a warp
-  // (reads that survive longer fetch their later blocks from L2)
+  // tiles; kSlotBlocksNarrow for the 256-bin tiles of q = 6, whose 128 KB
+  // tile leaves little room for the sixteen groups' slots of a warp -- the
+  // later blocks come from L2, and the warps that the smaller slots make
+  // room for hide that latency (1 block: 24 warps per SM; 7 blocks: 11)
   const uint32_t blocks = rv.ts / kBlockTokens;
   a.slot_blocks = ix.r4 <= 1024 ? blocks : min(blocks, kSlotBlocksNarrow);
   a.row_stride = a.slot_blocks * kBlockTokens * 2u;
