@@ -4,10 +4,10 @@
 //
 // GB300 mapping
 // -------------
-// * A persistent CTA (one per SM) takes work items (tile of TW*32 bins,
-//   range of reads).  The tile -- 4^q rows x TW words of the token-major
-//   table -- is staged in shared memory once per item and reused by every
-//   read of the range.  TW = 32 (1024 bins, 128 KB at q = 5) up to q = 5 and
+// * A persistent CTA (one per SM, up to 768 threads) takes work items (tile
+//   of TW*32 bins, range of reads).  The tile -- 4^q rows x TW words of the
+//   token-major table -- is staged in shared memory once per item and reused
+//   by every read of the range.  TW = 32 (1024 bins, 128 KB at q = 5) up to q = 5 and
 //   TW = 8 (256 bins, 128 KB) at q = 6.  Two extra rows follow the tile: all
 //   zeros (for a q-gram holding a non-base: always a miss) and all ones
 //   (padding after a read's last token: never a miss).
@@ -15,11 +15,17 @@
 //   group owns words 4i..4i+3 of the tile, i.e. 128 bins, and fetches them
 //   for each token with one 16-byte shared load.  At TW = 32 a quarter warp
 //   is one group reading one whole 128-byte row, so the four groups' loads of
-//   four rows are four conflict-free wavefronts; at TW = 8 four groups share
-//   a quarter warp and rows of 32 bytes can collide in a bank group.
+//   four rows are four conflict-free wavefronts; at TW = 8 sixteen groups
+//   load 32-byte rows whose bank group is row mod 4, and each group reads a
+//   block-rotated copy of its read's class-cyclic token order (see
+//   k_tokenise) so that every load covers the four bank groups evenly.
 // * Each group copies the token row of the read it will take next into its
 //   own shared-memory slot with cp.async while it works on the current one,
-//   so the inner loop never waits on global memory.
+//   so the inner loop does not wait on global memory.  At TW = 8 a slot
+//   holds only a read's first block (more warps fit beside the tile) and
+//   later blocks are loaded from L2.
+// * Reads are swept in ranges whose token rows fit in L2, range by range,
+//   so concurrent CTAs on different tiles share the same token rows.
 // * Instead of p separate counters, each lane keeps bit-sliced vertical
 //   counters: plane k of word w holds bit k of the counters of that word's 32
 //   bins.  Counted are MISSES (tokens absent from the bin), started at
