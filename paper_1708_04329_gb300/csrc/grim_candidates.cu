@@ -57,11 +57,11 @@ struct CandArgs {
 };
 
 constexpr int kWarps = 8;
-constexpr uint32_t kDefaultCandUnroll = 4;
-constexpr int kRegPlanes = 4;  // bit planes held in registers: multiplicities up to 15
+constexpr uint32_t kDefaultCandUnroll = 2;
+constexpr int kRegPlanes = 2;  // bit planes held in registers: multiplicities up to 3
 
 // per-warp shared memory: the multiplicity histogram, then bit planes
-// kRegPlanes..7 of the read (used only by reads with a token repeated 16+ times)
+// kRegPlanes..7 of the read (used only by reads with a token repeated 4+ times)
 __host__ __device__ constexpr uint32_t hist_words_of(uint32_t r4) { return r4 >= 4 ? r4 / 4 : 1; }
 __host__ __device__ constexpr uint32_t warp_smem_words(uint32_t r4, uint32_t wpb) {
   return hist_words_of(r4) + (8 - kRegPlanes) * wpb;
@@ -192,7 +192,7 @@ __device__ __forceinline__ uint32_t read_of(const uint64_t* __restrict__ cand_of
 }
 
 template <int WPB, int U>
-__global__ void __launch_bounds__(kWarps * 32, 4) k_candidates(CandArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, 6) k_candidates(CandArgs a) {
   using C = Cfg<WPB>;
   constexpr int WL = C::WL, G = C::G, CPW = C::CPW;
   extern __shared__ uint32_t s_warp[];
@@ -299,6 +299,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) k_candidates(CandArgs a) {
 template <int WPB, int U>
 void launch_u(const CandArgs& a, cudaStream_t st, const char* name) {
   const size_t smem = (size_t)kWarps * warp_smem_words(a.ix.r4, WPB) * sizeof(uint32_t);
+  cudaFuncSetAttribute(k_candidates<WPB, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
