@@ -135,6 +135,23 @@ template <int WPB, int WL>
 __device__ __forceinline__ uint32_t plane_sum(const uint32_t (&v)[WL],
                                               const uint32_t (&P)[kRegPlanes][WL], uint32_t K,
                                               const uint32_t* xplanes, uint32_t sub) {
+  if constexpr (WL == 4 && kRegPlanes == 2) {
+    if (K <= 2) {
+      // the eight masked words (four of weight 1, four of weight 2) summed
+      // bit-wise with a carry-save tree first: 4 POPC instead of 8
+      const uint32_t a0 = v[0] & P[0][0], a1 = v[1] & P[0][1], a2 = v[2] & P[0][2],
+                     a3 = v[3] & P[0][3];
+      const uint32_t b0 = v[0] & P[1][0], b1 = v[1] & P[1][1], b2 = v[2] & P[1][2],
+                     b3 = v[3] & P[1][3];
+      const uint32_t s1 = a0 ^ a1 ^ a2, c1 = (a0 & a1) | (a2 & (a0 ^ a1));  // weights 1, 2
+      const uint32_t s2 = s1 ^ a3, c2 = s1 & a3;                              // weights 1, 2
+      const uint32_t s3 = c1 ^ c2 ^ b0, c3 = (c1 & c2) | (b0 & (c1 ^ c2));   // weights 2, 4
+      const uint32_t s4 = b1 ^ b2 ^ b3, c4 = (b1 & b2) | (b3 & (b1 ^ b2));   // weights 2, 4
+      const uint32_t s5 = s3 ^ s4, c5 = s3 & s4;                              // weights 2, 4
+      const uint32_t s6 = c3 ^ c4 ^ c5, c6 = (c3 & c4) | (c5 & (c3 ^ c4));   // weights 4, 8
+      return __popc(s2) + 2u * __popc(s5) + 4u * __popc(s6) + 8u * __popc(c6);
+    }
+  }
   uint32_t sum = 0;
 #pragma unroll
   for (int p = 0; p < kRegPlanes; ++p) {
@@ -154,13 +171,15 @@ __device__ __forceinline__ uint32_t plane_sum(const uint32_t (&v)[WL],
   return sum;
 }
 
+// ids of candidates seg[off + u*CPW + slot] (u < U) of a segment of n
+// candidates, 0 past its end; 32-bit offsets within the segment
 template <int U, int CPW>
-__device__ __forceinline__ void load_ids(const int32_t* __restrict__ cand, uint64_t kb, uint64_t c1,
+__device__ __forceinline__ void load_ids(const int32_t* __restrict__ seg, uint32_t off, uint32_t n,
                                          uint32_t slot, uint32_t (&b)[U]) {
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const uint64_t k = kb + (uint64_t)u * CPW + slot;
-    b[u] = k < c1 ? (uint32_t)__ldg(cand + k) : 0u;
+    const uint32_t k = off + u * CPW + slot;
+    b[u] = k < n ? (uint32_t)__ldg(seg + k) : 0u;
   }
 }
 
@@ -215,7 +234,8 @@ __global__ void __launch_bounds__(kWarps * 32, 6) k_candidates(CandArgs a) {
 
   uint32_t cur = 0xFFFFFFFFu, K = 0, thr = 0;  // the read whose planes are built
   const bool check = a.check_ids;
-  const uint64_t last_row = a.ix.bm_rows - 1;
+  const uint32_t last_row = (uint32_t)(a.ix.bm_rows - 1);
+  const uint32_t num_bins = (uint32_t)a.ix.num_bins;  // bins are uint32 (checked at build)
   bool bad = false;  // this lane saw a candidate id outside [0, num_bins)
   uint32_t P[kRegPlanes][WL];
   // the next chunk is claimed one chunk ahead, so the atomic's latency
@@ -236,40 +256,42 @@ __global__ void __launch_bounds__(kWarps * 32, 6) k_candidates(CandArgs a) {
       // the end of the next read's list is fetched while this one is scored
       const uint64_t re_next = r + 2 <= n_reads && c1 < ce ? a.cand_off[r + 2] : re;
       if (c1 > pk) {
+        // the segment's candidates seg[0, n): offsets within it are 32-bit
+        const int32_t* seg = a.cand + pk;
+        const uint32_t n = (uint32_t)(c1 - pk);
         // the first candidate ids are fetched while the planes are built
         uint32_t bc[U];
-        load_ids<U, CPW>(a.cand, pk, c1, slot, bc);
+        load_ids<U, CPW>(seg, 0, n, slot, bc);
         if (r != cur) {
           cur = r;
           K = build_planes<WPB, WL>(a.rv, r, r4, hist, xplanes, lane, sub, P, &thr);
         }
         // U independent gathers in flight per lane group; the ids of the
         // next step are fetched before this step's vectors are used
-        for (uint64_t kb = pk; kb < c1; kb += (uint64_t)CPW * U) {
+        for (uint32_t off = 0; off < n; off += CPW * U) {
           uint32_t bn[U];
-          load_ids<U, CPW>(a.cand, kb + (uint64_t)CPW * U, c1, slot, bn);
+          load_ids<U, CPW>(seg, off + CPW * U, n, slot, bn);
           // the caller's ids are checked here, where they are read anyway: an
           // id outside [0, num_bins) fails the call, never passes, and its
           // gather is clamped inside the table
           uint32_t v[U][WL];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            const bool in = kb + (uint64_t)u * CPW + slot < c1;
-            bad |= check && in && bc[u] >= a.ix.num_bins;
-            const uint64_t row = min((uint64_t)bc[u], last_row);
-            if (in) load_words<WL>(a.ix.bm + row * WPB + sub * WL, v[u]);
+            const bool in = off + u * CPW + slot < n;
+            bad |= check && in && bc[u] >= num_bins;
+            const uint32_t row = min(bc[u], last_row);
+            if (in) load_words<WL>(a.ix.bm + (uint64_t)row * WPB + sub * WL, v[u]);
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
-            const uint64_t k = kb + (uint64_t)u * CPW + slot;
-            const bool valid = k < c1;
+            const uint32_t c = off + u * CPW + slot;
+            const bool valid = c < n;
             uint32_t sum = valid ? plane_sum<WPB, WL>(v[u], P, K, xplanes, sub) : 0u;
 #pragma unroll
             for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
             // bins past num_bins exist only as zero padding of the table
             // (members of the last super-bin); they never pass
-            const bool real = valid && bc[u] < a.ix.num_bins;
-            const bool pass = real && sub == 0 && sum >= thr;
+            const bool pass = valid && bc[u] < num_bins && sub == 0 && sum >= thr;
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
             if (bal) {
               unsigned long long base = 0;
@@ -278,7 +300,7 @@ __global__ void __launch_bounds__(kWarps * 32, 6) k_candidates(CandArgs a) {
               if (pass) {
                 const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
                 if (pos < a.rec.cap) {
-                  a.rec.keys[pos] = k;
+                  a.rec.keys[pos] = pk + c;
                   a.rec.counts[pos] = (uint8_t)sum;
                 }
               }
