@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
   __shared__ uint16_t s_row[kTokWarps][kMaxStride];
   __shared__ uint16_t s_seq[kTokWarps][kMaxStride];
   __shared__ uint8_t s_crank[kTokWarps][kMaxStride];
+  __shared__ uint8_t s_code[kTokWarps][kMaxStride + 16];  // per base: code | 4 if not a base
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t r = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   if (r >= live_reads(ctl, live, n_reads)) return;  // whole warps: warp syncs stay uniform
@@ -59,14 +60,21 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
     bad = true;
   }
   const uint32_t ntok = bad ? 0 : L - q + 1;
+  // each base read once (coalesced) and coded into shared memory
+  for (uint32_t i = lane; i < (bad ? 0u : L); i += 32) {
+    const uint32_t u = (uint8_t)reads[off + i] & 0xDFu;  // fold lowercase letters
+    const bool ok = (u == 0x41u) | (u == 0x43u) | (u == 0x47u) | (u == 0x54u);
+    s_code[warp][i] = (uint8_t)((((u >> 1) ^ (u >> 2)) & 3u) | (ok ? 0u : 4u));  // A0 C1 G2 T3
+  }
+  __syncwarp();
   for (uint32_t j = lane; j < ntok; j += 32) {
-    uint32_t v = 0;
-    bool clean = true;
+    uint32_t v = 0, flags = 0;
     for (uint32_t i = 0; i < q; ++i) {
-      const uint32_t u = (uint8_t)reads[off + j + i] & 0xDFu;  // fold lowercase letters
-      clean &= (u == 0x41u) | (u == 0x43u) | (u == 0x47u) | (u == 0x54u);
-      v = (v << 2) | (((u >> 1) ^ (u >> 2)) & 3u);  // A0 C1 G2 T3
+      const uint32_t c = s_code[warp][j + i];
+      v = (v << 2) | (c & 3u);
+      flags |= c;
     }
+    const bool clean = (flags & 4u) == 0;
     const uint32_t row = clean ? v : rowInvalid(r4);
     if (!presence && copies == 1) {  // no order wanted (candidate lists): positions as they are
       out[j] = (uint16_t)row;
