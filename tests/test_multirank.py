@@ -6,7 +6,6 @@ GPU work), so the test needs no GPU."""
 import os
 import socket
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
