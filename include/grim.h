@@ -178,6 +178,12 @@ const char* grim_strerror(int status);
 /* The CUDA error string behind the last GRIM_E_CUDA of the calling thread. */
 const char* grim_last_cuda_error(void);
 
+/* The build's scratch (packed reference) and the host-buffer entry points'
+ * device copies come from a library-owned stream-ordered memory pool per
+ * device that keeps freed memory for the next call.  This returns that
+ * cached memory of the current device to the driver.  Errors: GRIM_E_CUDA. */
+int grim_trim_scratch(void);
+
 /*
  * Bytes of device workspace grim_filter needs for n_reads reads, n_cand
  * candidates (0 in all-bins mode) and an output capacity of cap records.

@@ -146,6 +146,37 @@ int index_alloc(uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len, uin
 
 int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
 
+// A library-owned stream-ordered pool per device for the scratch of the
+// build and of the host-buffer entry points (packed reference, device copies
+// of host inputs, workspaces).  Its release threshold keeps freed memory
+// cached, so repeated calls do not map and unmap gigabytes each time, and it
+// leaves the process's default pool and its settings alone.
+cudaMemPool_t scratch_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> g(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool = scratch_pool();
+  if (!pool) return cudaMallocAsync(p, bytes, st);
+  return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
 
 void prof_suspend(bool on) { g_prof_suspended = on; }
 
@@ -218,6 +249,13 @@ const char* grim_strerror(int s) {
 
 const char* grim_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
+int grim_trim_scratch(void) {
+  cudaMemPool_t pool = scratch_pool();
+  if (!pool) return GRIM_OK;
+  const cudaError_t e = cudaMemPoolTrimTo(pool, 0);
+  return e == cudaSuccess ? GRIM_OK : cuda_fail(e);
+}
+
 int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
                uint32_t layouts, void* stream, grim_index** out) {
   return grim_build_ex(ref, len, B, q, max_read_len, layouts, nullptr, stream, out);
@@ -252,9 +290,9 @@ int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_
   // two-word reads of the token extraction)
   const uint64_t n32 = (len + 31) / 32;
   uint32_t *codes = nullptr, *invalid = nullptr;
-  e = cudaMallocAsync(&codes, (2 * n32 + 2) * sizeof(uint32_t), st);
+  e = scratch_alloc(reinterpret_cast<void**>(&codes), (2 * n32 + 2) * sizeof(uint32_t), st);
   if (e != cudaSuccess) return fail(cuda_fail(e));
-  e = cudaMallocAsync(&invalid, (n32 + 2) * sizeof(uint32_t), st);
+  e = scratch_alloc(reinterpret_cast<void**>(&invalid), (n32 + 2) * sizeof(uint32_t), st);
   if (e != cudaSuccess) {
     cudaFreeAsync(codes, st);
     return fail(cuda_fail(e));
@@ -267,7 +305,7 @@ int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_
   const bool transpose = v.q >= 5 && (ix->tm || ix->ctm);
   uint32_t* bm = ix->bm;
   if (!bm && transpose) {
-    e = cudaMallocAsync(&bm, bm_bins * v.wpb * sizeof(uint32_t), st);
+    e = scratch_alloc(reinterpret_cast<void**>(&bm), bm_bins * v.wpb * sizeof(uint32_t), st);
     if (e != cudaSuccess) {
       cudaFreeAsync(codes, st);
       cudaFreeAsync(invalid, st);
@@ -314,7 +352,7 @@ int grim_build_host_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q,
   if (!ref || len == 0) return GRIM_E_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* d = nullptr;
-  CK(cudaMallocAsync(&d, len, st));
+  CK(scratch_alloc(reinterpret_cast<void**>(&d), len, st));
   cudaError_t e = cudaMemcpyAsync(d, ref, len, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
     cudaFreeAsync(d, st);
@@ -531,7 +569,7 @@ int grim_filter_host(const grim_index* idx, const char* reads, const uint64_t* o
   const uint64_t o_ws = align256(o_oc + cap);
   const uint64_t total = o_ws + ws_bytes;
   char* d = nullptr;
-  CK(cudaMallocAsync(&d, total, st));
+  CK(scratch_alloc(reinterpret_cast<void**>(&d), total, st));
   auto h2d = [&](uint64_t o, const void* src, uint64_t n) {
     return n ? cudaMemcpyAsync(d + o, src, n, cudaMemcpyHostToDevice, st) : cudaSuccess;
   };

@@ -52,7 +52,7 @@ EXPORTS = (
     "grim_plan_wait", "grim_plan_device_bytes", "grim_plan_free", "grim_default_coarse_factor",
     "grim_server_create", "grim_server_submit", "grim_server_wait", "grim_server_take",
     "grim_server_stats_get", "grim_server_free", "grim_save", "grim_load",
-    "grim_reverse_complement", "grim_server_cancel",
+    "grim_reverse_complement", "grim_server_cancel", "grim_trim_scratch",
 )
 
 
@@ -183,6 +183,8 @@ def _lib() -> C.CDLL:
         lib.grim_plan_free.restype = None
         lib.grim_plan_free.argtypes = [vp]
         lib.grim_profile.restype = i32
+        lib.grim_trim_scratch.restype = i32
+        lib.grim_trim_scratch.argtypes = []
         lib.grim_reverse_complement.restype = i32
         lib.grim_reverse_complement.argtypes = [vp, vp, vp, u32, vp, vp]
         lib.grim_save.restype = i32
@@ -402,6 +404,13 @@ def grim_build_host_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GR
     if rc != GRIM_OK:
         raise GrimError(rc, "grim_build_host_ex")
     return GrimIndex(h.value)
+
+
+def grim_trim_scratch() -> None:
+    """Return the library's cached scratch memory of the current device."""
+    rc = _lib().grim_trim_scratch()
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_trim_scratch")
 
 
 def grim_save(index: GrimIndex, path) -> None:

@@ -83,3 +83,22 @@ def test_existence_sweep_small(world):
     by = {(r["q"], r["rate_pct"]): r["mean"] for r in rows}
     assert by[(4, 3)] >= by[(4, 0)] and by[(5, 3)] >= by[(5, 0)]
     assert by[(5, 0)] <= by[(4, 0)]
+
+
+def test_host_entry_points_reuse_and_trim_scratch(world):
+    """The host-buffer entry points give the same result call after call from
+    the library's cached scratch pool, and after the cache is trimmed."""
+    from paper_1708_04329_gb300 import grim, synth
+
+    g, oix, idx = world
+    rs = synth.reads(g, 200, seed=94, lengths=(100,), e=4, max_edits=4)
+    want = oracle.filter(oix, rs)
+    args = (np.frombuffer(rs.seq, np.uint8), rs.offsets, rs.lens, rs.e)
+    for _ in range(3):
+        assert_same(grim.grim_filter_host(idx, *args, cap=10_000), want)
+    grim.grim_trim_scratch()
+    assert_same(grim.grim_filter_host(idx, *args, cap=10_000), want)
+    idx2 = grim.grim_build_host(g, 100, 5, 100)
+    assert_same(grim.grim_filter_host(idx2, *args, cap=10_000), want)
+    grim.grim_trim_scratch()
+    idx2.close()
