@@ -178,6 +178,17 @@ const char* grim_strerror(int status);
 /* The CUDA error string behind the last GRIM_E_CUDA of the calling thread. */
 const char* grim_last_cuda_error(void);
 
+/* Device allocations of index tables through the caller's allocator (for
+ * example a framework's caching allocator, so the tables show in its
+ * accounting).  alloc returns `bytes` of device memory on the current
+ * device, or NULL (the build then fails with GRIM_E_NOMEM); free releases
+ * what alloc returned.  Both NULL restores cudaMalloc / cudaFree.  An index
+ * keeps the functions and ctx it was built with and frees its tables with
+ * them in grim_free.  Errors: GRIM_E_ARG (only one of the two given). */
+typedef void* (*grim_alloc_fn)(uint64_t bytes, void* ctx);
+typedef void (*grim_free_fn)(void* ptr, void* ctx);
+int grim_set_allocator(grim_alloc_fn alloc, grim_free_fn free, void* ctx);
+
 /* The build's scratch (packed reference) and the host-buffer entry points'
  * device copies come from a library-owned stream-ordered memory pool per
  * device that keeps freed memory for the next call.  This returns that

@@ -74,6 +74,12 @@ cudaEvent_t take_event() {
 
 }  // namespace
 
+// The caller's device allocator for index tables (grim_set_allocator).
+std::mutex g_alloc_mu;
+grim_alloc_fn g_alloc = nullptr;
+grim_free_fn g_free = nullptr;
+void* g_alloc_ctx = nullptr;
+
 // Validate an index's parameters and allocate its tables (contents not yet
 // written): token-major [4^q][num_bins_pad/32], bin-major padded with zero
 // vectors to whole super-bins, coarse token-major over super-bins of f bins,
@@ -110,25 +116,37 @@ int index_alloc(uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len, uin
   if (!ix) return GRIM_E_NOMEM;
   ix->layouts = layouts;
   ix->factor = f;
+  grim_alloc_fn alloc_fn;
+  {
+    std::lock_guard<std::mutex> g(g_alloc_mu);
+    alloc_fn = g_alloc;
+    ix->free_fn = g_free;
+    ix->alloc_ctx = g_alloc_ctx;
+  }
   auto fail = [&](cudaError_t e) {
     grim_free(ix);
     return cuda_fail(e);
   };
+  auto table = [&](uint32_t** p, uint64_t bytes) -> cudaError_t {
+    if (!alloc_fn) return cudaMalloc(p, bytes);
+    *p = static_cast<uint32_t*>(alloc_fn(bytes, ix->alloc_ctx));
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  };
   cudaError_t e;
   if (layouts & GRIM_LAYOUT_TOKEN_MAJOR) {
-    e = cudaMalloc(&ix->tm, (uint64_t)v.r4 * v.wpad * sizeof(uint32_t));
+    e = table(&ix->tm, (uint64_t)v.r4 * v.wpad * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(e);
   }
   if (layouts & GRIM_LAYOUT_BIN_MAJOR) {
-    e = cudaMalloc(&ix->bm, bm_bins * v.wpb * sizeof(uint32_t));
+    e = table(&ix->bm, bm_bins * v.wpb * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(e);
   }
   if (layouts & GRIM_LAYOUT_COARSE) {
-    e = cudaMalloc(&ix->ctm, (uint64_t)cv.r4 * cv.wpad * sizeof(uint32_t));
+    e = table(&ix->ctm, (uint64_t)cv.r4 * cv.wpad * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(e);
   }
   if (layouts & (GRIM_LAYOUT_COARSE | GRIM_LAYOUT_TOKEN_MAJOR)) {
-    e = cudaMalloc(&ix->presence, (uint64_t)v.r4 * sizeof(uint32_t));
+    e = table(&ix->presence, (uint64_t)v.r4 * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(e);
   }
   v.tm = ix->tm;
@@ -248,6 +266,15 @@ const char* grim_strerror(int s) {
 }
 
 const char* grim_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+int grim_set_allocator(grim_alloc_fn alloc, grim_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return GRIM_E_ARG;
+  std::lock_guard<std::mutex> g(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = alloc ? ctx : nullptr;
+  return GRIM_OK;
+}
 
 int grim_trim_scratch(void) {
   cudaMemPool_t pool = scratch_pool();
@@ -397,10 +424,11 @@ int grim_index_info(const grim_index* idx, grim_index_desc* out) {
 
 void grim_free(grim_index* idx) {
   if (!idx) return;
-  cudaFree(idx->tm);
-  cudaFree(idx->bm);
-  cudaFree(idx->ctm);
-  cudaFree(idx->presence);
+  for (uint32_t* p : {idx->tm, idx->bm, idx->ctm, idx->presence}) {
+    if (!p) continue;
+    if (idx->free_fn) idx->free_fn(p, idx->alloc_ctx);
+    else cudaFree(p);
+  }
   delete idx;
 }
 

@@ -264,6 +264,10 @@ struct grim_index {
   uint32_t* bm;
   uint32_t* ctm;
   uint32_t* presence;
+  // the allocator the tables came from (grim_set_allocator), or null for
+  // cudaMalloc / cudaFree
+  grim_free_fn free_fn;
+  void* alloc_ctx;
 };
 
 namespace grim {

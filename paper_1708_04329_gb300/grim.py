@@ -52,7 +52,7 @@ EXPORTS = (
     "grim_plan_wait", "grim_plan_device_bytes", "grim_plan_free", "grim_default_coarse_factor",
     "grim_server_create", "grim_server_submit", "grim_server_wait", "grim_server_take",
     "grim_server_stats_get", "grim_server_free", "grim_save", "grim_load",
-    "grim_reverse_complement", "grim_server_cancel", "grim_trim_scratch",
+    "grim_reverse_complement", "grim_server_cancel", "grim_trim_scratch", "grim_set_allocator",
 )
 
 
@@ -123,6 +123,10 @@ class _KTime(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_uint64), ("total_ms", C.c_double)]
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_ALLOCATOR = None  # the ctypes callbacks in use (kept alive here)
+
 _L = None
 
 
@@ -183,6 +187,8 @@ def _lib() -> C.CDLL:
         lib.grim_plan_free.restype = None
         lib.grim_plan_free.argtypes = [vp]
         lib.grim_profile.restype = i32
+        lib.grim_set_allocator.restype = i32
+        lib.grim_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, vp]
         lib.grim_trim_scratch.restype = i32
         lib.grim_trim_scratch.argtypes = []
         lib.grim_reverse_complement.restype = i32
@@ -404,6 +410,44 @@ def grim_build_host_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GR
     if rc != GRIM_OK:
         raise GrimError(rc, "grim_build_host_ex")
     return GrimIndex(h.value)
+
+
+def grim_set_allocator(alloc=None, free=None) -> None:
+    """Route index-table allocations through alloc(bytes) -> device pointer
+    and free(pointer); no arguments restores cudaMalloc / cudaFree."""
+    global _ALLOCATOR
+    if (alloc is None) != (free is None):
+        raise ValueError("give both alloc and free, or neither")
+    if alloc is None:
+        rc = _lib().grim_set_allocator(_ALLOC_FN(), _FREE_FN(), None)
+        _ALLOCATOR = None
+    else:
+        def _a(nbytes, _ctx):
+            try:
+                return int(alloc(int(nbytes))) or None
+            except Exception:
+                return None
+
+        def _f(ptr, _ctx):
+            free(int(ptr))
+
+        cbs = (_ALLOC_FN(_a), _FREE_FN(_f))
+        rc = _lib().grim_set_allocator(cbs[0], cbs[1], None)
+        if rc == GRIM_OK:
+            _ALLOCATOR = cbs
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_set_allocator")
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Index tables from PyTorch's caching allocator (they then count in
+    torch.cuda.memory_allocated), or back to cudaMalloc."""
+    if not enable:
+        grim_set_allocator()
+        return
+    torch = _torch()
+    grim_set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n),
+                       lambda p: torch.cuda.caching_allocator_delete(p))
 
 
 def grim_trim_scratch() -> None:

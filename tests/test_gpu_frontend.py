@@ -102,3 +102,33 @@ def test_host_entry_points_reuse_and_trim_scratch(world):
     assert_same(grim.grim_filter_host(idx2, *args, cap=10_000), want)
     grim.grim_trim_scratch()
     idx2.close()
+
+
+def test_index_tables_from_torch_allocator(world):
+    """With the allocator hook the index tables come from PyTorch's caching
+    allocator (they show in its accounting), filter identically, and go back
+    to it when the index is freed."""
+    from paper_1708_04329_gb300 import grim, synth
+
+    g, oix, _ = world
+    rs = synth.reads(g, 150, seed=95, lengths=(100,), e=4, max_edits=4)
+    want = oracle.filter(oix, rs)
+    ref = torch.from_numpy(g).cuda()
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    grim.use_torch_allocator()
+    try:
+        idx = grim.grim_build(ref, 100, 5, 100, 7)
+        d = idx.desc
+        tables = d.token_major_bytes + d.bin_major_bytes + d.coarse_token_major_bytes
+        assert torch.cuda.memory_allocated() - before >= tables
+        got = tuple(_host(x) for x in grim.grim_filter(idx, **dev_reads(rs)))
+        assert_same(got, want)
+        idx.close()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == before
+    finally:
+        grim.use_torch_allocator(False)
+    idx = grim.grim_build(ref, 100, 5, 100, 7)  # cudaMalloc again
+    assert_same(tuple(_host(x) for x in grim.grim_filter(idx, **dev_reads(rs))), want)
+    idx.close()
