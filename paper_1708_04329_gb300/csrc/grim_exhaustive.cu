@@ -42,10 +42,9 @@
 //   it runs on the FMA pipe instead.
 // * Early exit: after each 16-token block the group stops a read once every
 //   one of its 1024 bins is dead -- exact, since a dead bin can never pass.
-// * Groups advance independently (a finished group takes its next read of
-//   the range, dealt out statically) but stay converged: the per-block work
-//   is the same instruction stream for all groups, and every warp collective
-//   uses the full mask.
+// * Groups advance independently (a finished group takes the range's next
+//   read) but stay converged: the per-block work is the same instruction
+//   stream for all four groups, and every warp collective uses the full mask.
 #include "grim_internal.cuh"
 
 namespace grim {
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
   constexpr uint32_t kTileBinsT = TW * 32;
   // [tile: (r4 + 2) rows x TW words][group slots][16 padding tokens]
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_item, s_next;
   const uint32_t tid = threadIdx.x, lane = tid & 31, grp = lane / GL, li = lane % GL;
   const uint32_t nthreads = blockDim.x;
   const uint32_t r4 = a.ix.r4;
@@ -242,6 +241,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
     __syncthreads();  // previous item finished with the tile and the slots
     if (tid == 0) {
       s_item = atomicAdd(&a.ctl->item, 1u);
+      s_next = 0;
     }
     __syncthreads();
     const uint32_t item = s_item;
@@ -277,11 +277,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
     // per-group state (identical in the group's 8 lanes); the group's slot
     // holds two token rows: `buf` is the current read's, buf^1 the next's
     uint32_t cur = kNone, nxt = kNone, nxt_meta = 0, buf = 1;
-    const uint32_t n_groups = nthreads / GL;
-    // reads of the range are dealt out statically: group g takes g,
-    // g + n_groups, ... (no claim atomics in the read switches; with
-    // thousands of reads per group the groups finish close together)
-    uint32_t next_k = tid / GL;
     uint32_t nblk = 0, ntok = 0, bias = 0, executed = 0;
     bool fin = false;
     Counters<P> c;
@@ -289,8 +284,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
 
     // take the first read and start copying its tokens
     {
-      uint32_t k = next_k;
-      next_k += n_groups;
+      uint32_t k = 0;
+      if (li == 0) k = atomicAdd(&s_next, 1u);
+      k = __shfl_sync(0xFFFFFFFFu, k, grp * GL);
       if (k < nr) {
         nxt = r0 + k;
         nxt_meta = __ldg(a.rv.meta + nxt);
@@ -330,8 +326,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
         left = fin ? ~0u : nblk;
       }
       const bool take = need && !fin;
-      uint32_t k = next_k;
-      if (take) next_k += n_groups;
+      uint32_t k = 0;
+      if (take && li == 0) k = atomicAdd(&s_next, 1u);
+      k = __shfl_sync(0xFFFFFFFFu, k, grp * GL);
       if (take) {
         nxt = k < nr ? r0 + k : kNone;
         if (nxt != kNone) {
