@@ -191,8 +191,9 @@ int grim_set_allocator(grim_alloc_fn alloc, grim_free_fn free, void* ctx);
 
 /* The build's scratch (packed reference) and the host-buffer entry points'
  * device copies come from a library-owned stream-ordered memory pool per
- * device that keeps freed memory for the next call.  This returns that
- * cached memory of the current device to the driver.  Errors: GRIM_E_CUDA. */
+ * device that keeps freed memory for the next call.  This releases that
+ * cached memory of the current device (cudaMemPoolTrimTo).  Errors:
+ * GRIM_E_CUDA. */
 int grim_trim_scratch(void);
 
 /*
