@@ -132,3 +132,38 @@ def test_index_tables_from_torch_allocator(world):
     idx = grim.grim_build(ref, 100, 5, 100, 7)  # cudaMalloc again
     assert_same(tuple(_host(x) for x in grim.grim_filter(idx, **dev_reads(rs))), want)
     idx.close()
+
+
+def test_concurrent_calls_on_streams(world):
+    """The index is read-only: grim_filter calls from several host threads,
+    each on its own stream with its own workspace, give each caller the
+    same pass list as a call alone."""
+    import threading
+
+    from paper_1708_04329_gb300 import grim, synth
+
+    g, oix, idx = world
+    sets = [synth.reads(g, 120 + 40 * i, seed=96 + i, lengths=(100,), e=4, max_edits=4)
+            for i in range(4)]
+    want = [oracle.filter(oix, rs) for rs in sets]
+    errors = []
+
+    def worker(i):
+        try:
+            st = torch.cuda.Stream()
+            ws = grim.Workspace()
+            with torch.cuda.stream(st):
+                kw = dev_reads(sets[i])
+                for _ in range(5):
+                    got = grim.grim_filter(idx, **kw, workspace=ws, stream=st)
+                    st.synchronize()
+                    assert_same(tuple(_host(x) for x in got), want[i])
+        except Exception as exc:  # reported on the main thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=worker, args=(i,)) for i in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
