@@ -334,6 +334,11 @@ def run_native(args, rank, world, local):
                 "all_bins_filter_ms": round(all_bins_ms, 3),
                 "all_bins_method_tbit_per_s": round(method_bit_tests / (all_bins_ms / 1e3) / 1e12, 2),
                 "coarse_survivors": stats["survivors"]}
+    if roofline["traffic"]:
+        # DRAM GB/s of the dominant kernel (ncu traffic over its live time):
+        # the table is not the bound, the integer pipe is
+        roofline["dram_gbs"] = round(roofline["traffic"] / (per_launch_ms / 1e3) / 1e9, 2)
+        roofline["dram_frac_of_hbm"] = round(roofline["dram_gbs"] / float(peaks.get("hbm_gbs", 6800.0)), 5)
     stages = {k: round(v[1] / max(v[0], 1), 3) for k, v in prof.items()}
     launches = int(sum(v[0] for v in prof.values()))
     value = weak_value(rs.n, world, ms / args.steps)
