@@ -44,11 +44,23 @@ UNIT = "reads/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
 # launch of the dominant kernel, from a one-pass ncu capture of this
-# benchmark, keyed by the SHA-256 of the kernel source they were taken with:
-# a changed kernel reports null until it is measured again.
+# benchmark at its default sizes, keyed by the SHA-256 of the kernel source
+# they were taken with and by the workload: a changed kernel, another
+# workload or other sizes report null until measured.
 TRAFFIC = {
-    "dc4aaf2a1ca4a603": {"exhaustive_coarse": 7_050_000_000 + 284_390_000},
+    ("dc4aaf2a1ca4a603", "human"): {"exhaustive_coarse": 7_050_000_000 + 284_390_000},
 }
+
+
+DEFAULT_GENOME, DEFAULT_READS = 3_100_000_000, 1_000_000
+
+
+def traffic_for(args, dom: str):
+    if args.traffic is not None:
+        return args.traffic
+    if args.genome != DEFAULT_GENOME or args.reads != DEFAULT_READS:
+        return None
+    return TRAFFIC.get((kernel_sha(), args.workload), {}).get(dom)
 
 
 def parse_args():
@@ -67,8 +79,8 @@ def parse_args():
                         "mixed length and budget through one graph-captured plan")
     p.add_argument("--coarse-factor", type=int, default=0,
                    help="bins per super-bin of the coarse table (0: the library's choice)")
-    p.add_argument("--genome", type=int, default=3_100_000_000, help="reference length (bases)")
-    p.add_argument("--reads", type=int, default=1_000_000, help="reads per rank")
+    p.add_argument("--genome", type=int, default=DEFAULT_GENOME, help="reference length (bases)")
+    p.add_argument("--reads", type=int, default=DEFAULT_READS, help="reads per rank")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -324,7 +336,7 @@ def run_native(args, rank, world, local):
     method_bit_tests = rs.n * nb * ntok
     roofline = {"bound": "alu", "achieved": round(achieved_tbit, 2), "peak": round(peak_tbit, 2),
                 "unit": "Tbit-tests/s", "frac": round(achieved_tbit / peak_tbit, 4),
-                "traffic": args.traffic if args.traffic is not None else TRAFFIC.get(kernel_sha(), {}).get(dom),
+                "traffic": traffic_for(args, dom),
                 "kernel": f"k_exhaustive ({'super-bins' if dom == 'exhaustive_coarse' else 'bins'})",
                 "kernel_ms": round(per_launch_ms, 3),
                 "peak_basis": f"{n_sm} SMs x 128 B/clk shared-memory loads x 8 bits x {sm_max:.0f} MHz",
@@ -488,7 +500,7 @@ def run_ragged(args, rank, world, local):
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    n_reads = args.reads if args.reads != 1_000_000 else 4_000_000
+    n_reads = args.reads if args.reads != DEFAULT_READS else 4_000_000
     t0 = time.perf_counter()
     g = synth.human_genome(args.genome)
     w = synth.ragged_candidates(n_reads=n_reads, g=g)
@@ -589,12 +601,66 @@ def run_ragged(args, rank, world, local):
                      "frac": round(gbytes / (kernel_ms / 1e3) / hbm, 4), "traffic": None,
                      "algorithmic_bytes": round(gbytes * 1e9)},
     }
+    ceiling = gather_ceiling(nb, vec_bytes, n_cand, st)
+    if ceiling.get("gbs"):
+        ceiling["frac_of_hbm"] = round(ceiling["gbs"] / hbm, 4)
+    line["gather_ceiling"] = ceiling
+    if ceiling.get("rows_per_s"):
+        line["roofline"]["frac_of_gather_ceiling"] = round(
+            n_cand / (kernel_ms / 1e3) / ceiling["rows_per_s"], 4)
     plan.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def gather_ceiling(rows: int, row_bytes: int, n: int, st, warmup: int = 3, reps: int = 5) -> dict:
+    """The random-gather rate of this GPU on a table shaped like the bin-major
+    table (rows x row_bytes, random rows, no ids, no arithmetic): the ceiling
+    of any kernel that gathers one bin vector per candidate.  Timed with CUDA
+    events on the launching stream; the best of unroll 1, 2, 4 is reported."""
+    import ctypes
+
+    import torch
+
+    if row_bytes not in (128, 512):
+        return {"unavailable": f"no probe for {row_bytes}-byte rows"}
+    lib = ctypes.CDLL(str(ROOT / "paper_1708_04329_gb300" / "_lib" / "libgrim_probe.so"))
+    lib.grim_probe_gather.restype = ctypes.c_int
+    lib.grim_probe_gather.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                      ctypes.c_uint64, ctypes.c_void_p]
+    lib.grim_probe_gather_sink_words.restype = ctypes.c_uint64
+    table = torch.randint(-2 ** 31, 2 ** 31 - 1, (rows * row_bytes // 4,), dtype=torch.int32,
+                          device="cuda")
+    words = int(lib.grim_probe_gather_sink_words())
+    sink = torch.empty(max(words, 1), dtype=torch.int32, device="cuda")
+    best = None
+    for u in (1, 2, 4):
+        def launch():
+            rc = lib.grim_probe_gather(table.data_ptr(), rows, row_bytes, n, u, sink.data_ptr(),
+                                       words, ctypes.c_void_p(st.cuda_stream))
+            if rc != 0:
+                raise RuntimeError(f"grim_probe_gather failed: {rc}")
+        for _ in range(warmup):
+            launch()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(st)
+        for _ in range(reps):
+            launch()
+        b.record(st)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        if best is None or ms < best[1]:
+            best = (u, ms)
+    del table, sink
+    u, ms = best
+    return {"kernel": "k_probe_gather", "row_bytes": row_bytes, "rows": rows, "gathers": n,
+            "unroll": u, "ms": round(ms, 3), "rows_per_s": round(n / (ms / 1e3), 1),
+            "gbs": round(n * row_bytes / (ms / 1e3) / 1e9, 1)}
 
 
 # ---------------------------------------------------------------------------

@@ -210,8 +210,10 @@ __device__ __forceinline__ uint32_t read_of(const uint64_t* __restrict__ cand_of
   return lo;
 }
 
+// Eight CTAs per SM (64 warps, 32 registers a thread): the gathers are
+// latency-bound, and the extra warps outweigh a few spilled words.
 template <int WPB, int U>
-__global__ void __launch_bounds__(kWarps * 32, 6) k_candidates(CandArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, 8) k_candidates(CandArgs a) {
   using C = Cfg<WPB>;
   constexpr int WL = C::WL, G = C::G, CPW = C::CPW;
   extern __shared__ uint32_t s_warp[];
@@ -246,19 +248,23 @@ __global__ void __launch_bounds__(kWarps * 32, 6) k_candidates(CandArgs a) {
     const uint32_t cj = __shfl_sync(0xFFFFFFFFu, cj_next, 0);
     if (cj >= n_chunks) break;
     if (lane == 0) cj_next = atomicAdd(&a.ctl->item, 1u);
-    uint64_t pk = c_begin + (uint64_t)cj * chunk;
-    const uint64_t ce = min(pk + chunk, c_end);
-    uint32_t r = read_of(a.cand_off, n_reads, pk, lane);
-    uint64_t re = a.cand_off[r + 1];
-    while (pk < ce) {
-      // the segment [pk, c1) of read r's list inside this chunk
-      const uint64_t c1 = min(re, ce);
-      // the end of the next read's list is fetched while this one is scored
-      const uint64_t re_next = r + 2 <= n_reads && c1 < ce ? a.cand_off[r + 2] : re;
-      if (c1 > pk) {
-        // the segment's candidates seg[0, n): offsets within it are 32-bit
-        const int32_t* seg = a.cand + pk;
-        const uint32_t n = (uint32_t)(c1 - pk);
+    // positions inside the chunk are 32-bit, relative to its first candidate
+    const uint64_t base = c_begin + (uint64_t)cj * chunk;
+    const uint32_t clen = (uint32_t)min(chunk, c_end - base);
+    uint32_t r = read_of(a.cand_off, n_reads, base, lane);
+    // the end of read r's list, clipped to the chunk (> 0: r's list holds base)
+    uint32_t c1 = (uint32_t)min(a.cand_off[r + 1] - base, (uint64_t)clen);
+    uint32_t p = 0;
+    while (p < clen) {
+      // the segment [p, c1) of read r's list inside this chunk; the end of the
+      // next read's list is fetched while this one is scored
+      const uint32_t c1_next = r + 2 <= n_reads && c1 < clen
+                                   ? (uint32_t)min(a.cand_off[r + 2] - base, (uint64_t)clen)
+                                   : c1;
+      if (c1 > p) {
+        // the segment's candidates seg[0, n)
+        const int32_t* seg = a.cand + base + p;
+        const uint32_t n = c1 - p;
         // the first candidate ids are fetched while the planes are built
         uint32_t bc[U];
         load_ids<U, CPW>(seg, 0, n, slot, bc);
@@ -294,13 +300,13 @@ __global__ void __launch_bounds__(kWarps * 32, 6) k_candidates(CandArgs a) {
             const bool pass = valid && bc[u] < num_bins && sub == 0 && sum >= thr;
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
             if (bal) {
-              unsigned long long base = 0;
-              if (lane == 0) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)__popc(bal));
-              base = __shfl_sync(0xFFFFFFFFu, base, 0);
+              unsigned long long first = 0;  // the warp's first record slot
+              if (lane == 0) first = atomicAdd(&a.ctl->n_rec, (unsigned long long)__popc(bal));
+              first = __shfl_sync(0xFFFFFFFFu, first, 0);
               if (pass) {
-                const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+                const unsigned long long pos = first + __popc(bal & ((1u << lane) - 1u));
                 if (pos < a.rec.cap) {
-                  a.rec.keys[pos] = pk + c;
+                  a.rec.keys[pos] = base + p + c;
                   a.rec.counts[pos] = (uint8_t)sum;
                 }
               }
@@ -310,9 +316,9 @@ __global__ void __launch_bounds__(kWarps * 32, 6) k_candidates(CandArgs a) {
           for (int u = 0; u < U; ++u) bc[u] = bn[u];
         }
       }
-      pk = c1;
+      p = c1;
       ++r;
-      re = re_next;
+      c1 = c1_next;
     }
   }
   if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(&a.ctl->status, kStatusBadCand);

@@ -78,3 +78,15 @@ def C_void():
     import ctypes
 
     return ctypes.byref(ctypes.c_void_p())
+
+
+def test_gather_probe_library_exports():
+    """The benchmark's random-gather probe (a measurement helper beside the
+    filter) builds and exports its two entry points."""
+    from paper_1708_04329_gb300 import _build
+
+    path = _build.build_probe()
+    out = subprocess.run(["nm", "-D", "--defined-only", str(path)], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert {"grim_probe_gather", "grim_probe_gather_sink_words"} <= exported
