@@ -365,6 +365,23 @@ def run_native(args, rank, world, local):
         "kernel_ms_per_launch": stages,
         "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
     }
+    if rank == 0 and args.workload == "finer" and "candidates" in stages:
+        # the candidate leg: 512-byte vector gathers, against the copy
+        # bandwidth and against this GPU's random-gather ceiling for such rows
+        vec = 4 ** q // 8
+        n_cand = len(w["cand"])
+        k_ms = stages["candidates"]
+        gbytes = n_cand * (vec + 4) / 1e9
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        leg = {"bound": "hbm", "kernel": "k_candidates", "kernel_ms": k_ms,
+               "algorithmic_bytes": round(gbytes * 1e9), "achieved": round(gbytes / (k_ms / 1e3), 1),
+               "peak": hbm, "unit": "GB/s", "frac": round(gbytes / (k_ms / 1e3) / hbm, 4)}
+        ceiling = gather_ceiling(nb, vec, n_cand, st)
+        if ceiling.get("gbs"):
+            ceiling["frac_of_hbm"] = round(ceiling["gbs"] / hbm, 4)
+            leg["frac_of_gather_ceiling"] = round(n_cand / (k_ms / 1e3) / ceiling["rows_per_s"], 4)
+        leg["gather_ceiling"] = ceiling
+        line["candidate_roofline"] = leg
     if rank == 0 and not args.no_e2e:
         line["e2e"] = run_e2e(args, w, st)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -57,7 +57,10 @@ struct CandArgs {
 };
 
 constexpr int kWarps = 8;
-constexpr uint32_t kDefaultCandUnroll = 2;
+// gathers in flight per lane group when the caller leaves it to the library:
+// two for vectors up to 128 bytes, four for 512-byte vectors (q = 6), as
+// the autotuner measured on GB300
+constexpr uint32_t default_cand_unroll(uint32_t wpb) { return wpb >= 128 ? 4u : 2u; }
 constexpr int kRegPlanes = 2;  // bit planes held in registers: multiplicities up to 3
 
 // per-warp shared memory: the multiplicity histogram, then bit planes
@@ -210,10 +213,14 @@ __device__ __forceinline__ uint32_t read_of(const uint64_t* __restrict__ cand_of
   return lo;
 }
 
-// Eight CTAs per SM (64 warps, 32 registers a thread): the gathers are
-// latency-bound, and the extra warps outweigh a few spilled words.
+// CTAs per SM.  Up to 128-byte vectors: eight (64 warps, 32 registers a
+// thread); the gathers are latency-bound, and the extra warps outweigh a few
+// spilled words.  512-byte vectors (q = 6): six (40 registers), where the
+// spills of the 32-register layout cost more than the warps gain.
+__host__ __device__ constexpr int cand_ctas_per_sm(int wpb) { return wpb >= 128 ? 6 : 8; }
+
 template <int WPB, int U>
-__global__ void __launch_bounds__(kWarps * 32, 8) k_candidates(CandArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, cand_ctas_per_sm(WPB)) k_candidates(CandArgs a) {
   using C = Cfg<WPB>;
   constexpr int WL = C::WL, G = C::G, CPW = C::CPW;
   extern __shared__ uint32_t s_warp[];
@@ -352,7 +359,7 @@ void launch_t(const CandArgs& a, cudaStream_t st, const char* name, uint32_t unr
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
                        const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
                        const char* prof_name, Live live, uint32_t unroll, bool check_ids) {
-  if (unroll == 0) unroll = kDefaultCandUnroll;
+  if (unroll == 0) unroll = default_cand_unroll(ix.wpb);
   if (rv.n_reads == 0) return;
   CandArgs a{ix, rv, cand, cand_off, rec, ctl, live, check_ids};
   switch (ix.wpb) {
