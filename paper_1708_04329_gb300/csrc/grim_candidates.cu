@@ -174,6 +174,28 @@ __device__ __forceinline__ uint32_t plane_sum(const uint32_t (&v)[WL],
   return sum;
 }
 
+// Sums of U candidates over a lane group of G lanes (U <= G, powers of two):
+// at each of the first log2(U) butterfly steps a lane keeps half of its
+// sums and adds its partner's copy of them, sending the other half; the
+// remaining steps reduce the one sum left.  Lane `sub` of the group returns
+// the group total of candidate sub / (G / U).  log2(U) + log2(G/U) shuffles
+// instead of U * log2(G).
+template <int G, int U>
+__device__ __forceinline__ uint32_t reduce_scatter(uint32_t (&s)[U], uint32_t sub) {
+#pragma unroll
+  for (int n = U, m = G / 2; n > 1; n >>= 1, m >>= 1) {
+    const bool upper = (sub & (uint32_t)m) != 0;  // keep the upper half of the n sums
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const uint32_t lo = s[i], hi = s[i + n / 2];
+      s[i] = (upper ? hi : lo) + __shfl_xor_sync(0xFFFFFFFFu, upper ? lo : hi, m);
+    }
+  }
+#pragma unroll
+  for (int m = G / (2 * U); m >= 1; m >>= 1) s[0] += __shfl_xor_sync(0xFFFFFFFFu, s[0], m);
+  return s[0];
+}
+
 // ids of candidates seg[off + u*CPW + slot] (u < U) of a segment of n
 // candidates, 0 past its end; 32-bit offsets within the segment
 template <int U, int CPW>
@@ -295,16 +317,8 @@ __global__ void __launch_bounds__(kWarps * 32, cand_ctas_per_sm(WPB)) k_candidat
             const uint32_t row = min(bc[u], last_row);
             if (in) load_words<WL>(a.ix.bm + (uint64_t)row * WPB + sub * WL, v[u]);
           }
-#pragma unroll
-          for (int u = 0; u < U; ++u) {
-            const uint32_t c = off + u * CPW + slot;
-            const bool valid = c < n;
-            uint32_t sum = valid ? plane_sum<WPB, WL>(v[u], P, K, xplanes, sub) : 0u;
-#pragma unroll
-            for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
-            // bins past num_bins exist only as zero padding of the table
-            // (members of the last super-bin); they never pass
-            const bool pass = valid && bc[u] < num_bins && sub == 0 && sum >= thr;
+          // passing candidates of the warp get consecutive record slots
+          auto emit = [&](bool pass, uint32_t c, uint32_t sum) {
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, pass);
             if (bal) {
               unsigned long long first = 0;  // the warp's first record slot
@@ -317,6 +331,32 @@ __global__ void __launch_bounds__(kWarps * 32, cand_ctas_per_sm(WPB)) k_candidat
                   a.rec.counts[pos] = (uint8_t)sum;
                 }
               }
+            }
+          };
+          uint32_t sums[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u)
+            sums[u] = off + u * CPW + slot < n ? plane_sum<WPB, WL>(v[u], P, K, xplanes, sub) : 0u;
+          // bins past num_bins exist only as zero padding of the table
+          // (members of the last super-bin); they never pass
+          if constexpr (U > 1 && U <= G) {
+            // the U sums reduced over the lane group at once: each lane ends
+            // with the total of candidate uq, held by G/U lanes
+            const uint32_t total = reduce_scatter<G, U>(sums, sub);
+            const uint32_t uq = sub / (G / U);
+            uint32_t id = bc[0];
+#pragma unroll
+            for (int u = 1; u < U; ++u) id = uq == (uint32_t)u ? bc[u] : id;
+            const uint32_t c = off + uq * CPW + slot;
+            emit(sub % (G / U) == 0 && c < n && id < num_bins && total >= thr, c, total);
+          } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const uint32_t c = off + u * CPW + slot;
+              uint32_t sum = sums[u];
+#pragma unroll
+              for (int o = G / 2; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+              emit(c < n && bc[u] < num_bins && sub == 0 && sum >= thr, c, sum);
             }
           }
 #pragma unroll
