@@ -414,18 +414,26 @@ def run_e2e(args, w, st):
     outs = [tuple(torch.empty(cap, dtype=dt).pin_memory() for dt in (torch.int32, torch.int32, torch.uint8))
             for _ in range(2)]
     nout = {}
+    phases = np.zeros(4)  # host time of each call: build, all-bins, candidates, free
 
     def step():
+        t = [time.perf_counter()]
         idx = grim.grim_build_host_ex(h["ref"], w["B"], w["q"], w["max_read_len"],
                                       coarse_factor=args.coarse_factor, stream=st)
+        t.append(time.perf_counter())
         a = grim.grim_filter_host(idx, h["seq"], h["off"], h["lens"], h["e"], out=outs[0], stream=st)
+        t.append(time.perf_counter())
         b = grim.grim_filter_host(idx, h["seq"], h["off"], h["lens"], h["e"], cand=h["cand"],
                                   cand_off=h["coff"], out=outs[1], stream=st)
+        t.append(time.perf_counter())
         nout["a"], nout["b"] = len(a[0]), len(b[0])
         idx.close()
+        t.append(time.perf_counter())
+        phases[:] += np.diff(t)
 
     step()  # warm the stream-ordered pool
     torch.cuda.synchronize()
+    phases[:] = 0
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         step()
@@ -436,7 +444,9 @@ def run_e2e(args, w, st):
     d2h = 9 * (nout["a"] + nout["b"])
     return {"value": round(rs.n / dt, 1), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 3),
-            "steps": args.e2e_steps}
+            "steps": args.e2e_steps,
+            "phases_ms": dict(zip(("build_host", "all_bins_host", "candidates_host", "free"),
+                                  (round(float(x) * 1e3 / args.e2e_steps, 2) for x in phases)))}
 
 
 # ---------------------------------------------------------------------------
