@@ -57,29 +57,40 @@ struct CandArgs {
 };
 
 constexpr int kWarps = 8;
-// gathers in flight per lane group when the caller leaves it to the library:
-// two for vectors up to 128 bytes, four for 512-byte vectors (q = 6), as
-// the autotuner measured on GB300
-constexpr uint32_t default_cand_unroll(uint32_t wpb) { return wpb >= 128 ? 4u : 2u; }
+// gathers in flight per lane group when the caller leaves it to the library
+// (the autotuner's choice on GB300 for both 128- and 512-byte vectors)
+constexpr uint32_t kDefaultCandUnroll = 2;
 constexpr int kRegPlanes = 2;  // bit planes held in registers: multiplicities up to 3
 
-// per-warp shared memory: the multiplicity histogram, then bit planes
-// kRegPlanes..7 of the read (used only by reads with a token repeated 4+ times)
+// Multiplicities of 4 and more (bits kRegPlanes.. of a token's count) are
+// rare.  Up to 128-byte vectors they are kept as further bit planes in shared
+// memory (xplanes[k - kRegPlanes][word]).  For 512-byte vectors those planes
+// would take 3 KB a warp beside the 4 KB histogram and limit the kernel to
+// 32 warps per SM; instead the read's tokens of multiplicity >= 4 are listed
+// (token | (mult & ~3) << 16; at most 255 / 4 < 64 of them) and added one by
+// one, which makes room for 48 warps.
+template <int WPB> __host__ __device__ constexpr bool heavy_list() { return WPB >= 128; }
+constexpr uint32_t kMaxHeavy = 64;
+
+// per-warp shared memory: the multiplicity histogram, then the higher bit
+// planes or the list of heavy tokens
 __host__ __device__ constexpr uint32_t hist_words_of(uint32_t r4) { return r4 >= 4 ? r4 / 4 : 1; }
 __host__ __device__ constexpr uint32_t warp_smem_words(uint32_t r4, uint32_t wpb) {
-  return hist_words_of(r4) + (8 - kRegPlanes) * wpb;
+  return hist_words_of(r4) + (wpb >= 128 ? kMaxHeavy : (8 - kRegPlanes) * wpb);
 }
 
 // The read's multiplicity histogram (byte t = how many of its positions hold
 // token t) and its bit planes P_k = {t : bit k of mult(t)} for this lane's WL
 // words of a bin vector: planes below kRegPlanes in registers, the rest in
-// shared memory (xplanes[k - kRegPlanes][word]).  Returns K, the number of
-// planes in use, and the read's threshold in *thr.  Warp-collective.
+// shared memory, or (heavy_list) the heavy tokens in xplanes[0, *nh).
+// Returns K, the number of planes in use, and the read's threshold in *thr.
+// Warp-collective.
 template <int WPB, int WL>
 __device__ __forceinline__ uint32_t build_planes(const ReadsView& rv, uint32_t r, uint32_t r4,
                                                  uint32_t* hist, uint32_t* xplanes, uint32_t lane,
                                                  uint32_t sub, uint32_t (&P)[kRegPlanes][WL],
-                                                 uint32_t* thr) {
+                                                 uint32_t* thr, uint32_t* nh) {
+  constexpr int kPlanesBuilt = heavy_list<WPB>() ? kRegPlanes : 8;
   const uint32_t hist_words = hist_words_of(r4);
   // the warp has finished reading the previous read's histogram
   __syncwarp();
@@ -112,7 +123,7 @@ __device__ __forceinline__ uint32_t build_planes(const ReadsView& rv, uint32_t r
       hw[j] = h < hist_words && (wi * 32 + 4 * j) < r4 ? hist[h] : 0u;
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < kPlanesBuilt; ++k) {
       if ((uint32_t)k < K) {
         uint32_t pk = 0;
 #pragma unroll
@@ -129,17 +140,51 @@ __device__ __forceinline__ uint32_t build_planes(const ReadsView& rv, uint32_t r
       }
     }
   }
+  if constexpr (heavy_list<WPB>()) {
+    uint32_t count = 0;
+    if (K > (uint32_t)kRegPlanes) {
+      // list the tokens of multiplicity >= 4 with the part of their count
+      // above the register planes; each lane takes its histogram words
+      uint32_t mine = 0;
+      for (uint32_t i = lane; i < hist_words; i += 32) {
+        const uint32_t h = hist[i];
+        mine += ((h & 0xFCu) != 0) + ((h & 0xFC00u) != 0) + ((h & 0xFC0000u) != 0) +
+                ((h & 0xFC000000u) != 0);
+      }
+      uint32_t incl = mine;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= (uint32_t)d) incl += t;
+      }
+      count = __shfl_sync(0xFFFFFFFFu, incl, 31);
+      uint32_t pos = incl - mine;
+      for (uint32_t i = lane; i < hist_words; i += 32) {
+        const uint32_t h = hist[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t mult = (h >> (8 * j)) & 0xFFu;
+          if (mult >= 4 && pos < kMaxHeavy) xplanes[pos++] = (4 * i + j) | ((mult & ~3u) << 16);
+        }
+      }
+      __syncwarp();
+    }
+    *nh = min(count, kMaxHeavy);
+  }
   *thr = ntok - dmax;  // pass iff sum >= (L-q+1) - min(q*e, L-q+1)
   return K;
 }
 
-// sum_k 2^k popc(v & P_k) over this lane's WL words
+// sum_k 2^k popc(v & P_k) over this lane's WL words (with heavy_list: the
+// two register planes, then the listed heavy tokens that fall in this
+// lane's words, nh of them)
 template <int WPB, int WL>
 __device__ __forceinline__ uint32_t plane_sum(const uint32_t (&v)[WL],
                                               const uint32_t (&P)[kRegPlanes][WL], uint32_t K,
-                                              const uint32_t* xplanes, uint32_t sub) {
+                                              const uint32_t* xplanes, uint32_t sub, uint32_t nh) {
+  static_assert(!heavy_list<WPB>() || (WL == 4 && kRegPlanes == 2), "heavy list layout");
   if constexpr (WL == 4 && kRegPlanes == 2) {
-    if (K <= 2) {
+    if (heavy_list<WPB>() || K <= 2) {
       // the eight masked words (four of weight 1, four of weight 2) summed
       // bit-wise with a carry-save tree first: 4 POPC instead of 8
       const uint32_t a0 = v[0] & P[0][0], a1 = v[1] & P[0][1], a2 = v[2] & P[0][2],
@@ -152,7 +197,19 @@ __device__ __forceinline__ uint32_t plane_sum(const uint32_t (&v)[WL],
       const uint32_t s4 = b1 ^ b2 ^ b3, c4 = (b1 & b2) | (b3 & (b1 ^ b2));   // weights 2, 4
       const uint32_t s5 = s3 ^ s4, c5 = s3 & s4;                              // weights 2, 4
       const uint32_t s6 = c3 ^ c4 ^ c5, c6 = (c3 & c4) | (c5 & (c3 ^ c4));   // weights 4, 8
-      return __popc(s2) + 2u * __popc(s5) + 4u * __popc(s6) + 8u * __popc(c6);
+      uint32_t sum = __popc(s2) + 2u * __popc(s5) + 4u * __popc(s6) + 8u * __popc(c6);
+      if constexpr (heavy_list<WPB>()) {
+        for (uint32_t i = 0; i < nh; ++i) {
+          const uint32_t ent = xplanes[i];
+          const uint32_t t = ent & 0xFFFFu, wi = t >> 5;  // token, word of the vector
+          if (wi / WL == sub) {
+            const uint32_t w = wi % WL;
+            const uint32_t word = w == 0 ? v[0] : w == 1 ? v[1] : w == 2 ? v[2] : v[3];
+            sum += ((word >> (t & 31u)) & 1u) * (ent >> 16);
+          }
+        }
+      }
+      return sum;
     }
   }
   uint32_t sum = 0;
@@ -249,7 +306,7 @@ __global__ void __launch_bounds__(kWarps * 32, cand_ctas_per_sm(WPB)) k_candidat
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t r4 = a.ix.r4;
   uint32_t* hist = s_warp + warp * warp_smem_words(r4, WPB);  // byte t = multiplicity of token t
-  uint32_t* xplanes = hist + hist_words_of(r4);                 // [8 - kRegPlanes][WPB]
+  uint32_t* xplanes = hist + hist_words_of(r4);  // higher planes or heavy tokens
   const uint32_t sub = lane % G;     // this lane's slice of a bin vector
   const uint32_t slot = lane / G;    // which of the warp's CPW candidates
   if (*(volatile uint32_t*)&a.ctl->status) return;
@@ -263,7 +320,7 @@ __global__ void __launch_bounds__(kWarps * 32, cand_ctas_per_sm(WPB)) k_candidat
       c_end > c_begin ? chunk_size(c_end - c_begin, (uint64_t)gridDim.x * kWarps) : kChunkMin;
   const uint64_t n_chunks = c_end > c_begin ? (c_end - c_begin + chunk - 1) / chunk : 0;
 
-  uint32_t cur = 0xFFFFFFFFu, K = 0, thr = 0;  // the read whose planes are built
+  uint32_t cur = 0xFFFFFFFFu, K = 0, thr = 0, nh = 0;  // the read whose planes are built
   const bool check = a.check_ids;
   const uint32_t last_row = (uint32_t)(a.ix.bm_rows - 1);
   const uint32_t num_bins = (uint32_t)a.ix.num_bins;  // bins are uint32 (checked at build)
@@ -299,7 +356,7 @@ __global__ void __launch_bounds__(kWarps * 32, cand_ctas_per_sm(WPB)) k_candidat
         load_ids<U, CPW>(seg, 0, n, slot, bc);
         if (r != cur) {
           cur = r;
-          K = build_planes<WPB, WL>(a.rv, r, r4, hist, xplanes, lane, sub, P, &thr);
+          K = build_planes<WPB, WL>(a.rv, r, r4, hist, xplanes, lane, sub, P, &thr, &nh);
         }
         // U independent gathers in flight per lane group; the ids of the
         // next step are fetched before this step's vectors are used
@@ -336,7 +393,7 @@ __global__ void __launch_bounds__(kWarps * 32, cand_ctas_per_sm(WPB)) k_candidat
           uint32_t sums[U];
 #pragma unroll
           for (int u = 0; u < U; ++u)
-            sums[u] = off + u * CPW + slot < n ? plane_sum<WPB, WL>(v[u], P, K, xplanes, sub) : 0u;
+            sums[u] = off + u * CPW + slot < n ? plane_sum<WPB, WL>(v[u], P, K, xplanes, sub, nh) : 0u;
           // bins past num_bins exist only as zero padding of the table
           // (members of the last super-bin); they never pass
           if constexpr (U > 1 && U <= G) {
@@ -399,7 +456,7 @@ void launch_t(const CandArgs& a, cudaStream_t st, const char* name, uint32_t unr
 void launch_candidates(const IndexView& ix, const ReadsView& rv, const int32_t* cand,
                        const uint64_t* cand_off, RecordsView rec, Ctl* ctl, cudaStream_t st,
                        const char* prof_name, Live live, uint32_t unroll, bool check_ids) {
-  if (unroll == 0) unroll = default_cand_unroll(ix.wpb);
+  if (unroll == 0) unroll = kDefaultCandUnroll;
   if (rv.n_reads == 0) return;
   CandArgs a{ix, rv, cand, cand_off, rec, ctl, live, check_ids};
   switch (ix.wpb) {

@@ -323,3 +323,65 @@ def test_coarse_factors(q, factor):
     idx, oix = _check_tables(_np(ref), B, q, mrl, layouts=6, factor=factor)
     assert idx.desc.coarse_factor == factor
     assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
+
+
+def _low_complexity_case(rng, n: int, n_reads: int, mrl: int):
+    """A genome with homopolymer and short tandem-repeat blocks, and reads
+    drawn from them (or made of such repeats): tokens of high multiplicity,
+    up to L-q+1 copies of one token."""
+    alpha = np.frombuffer(b"ACGT", dtype=np.uint8)
+    g = alpha[rng.integers(0, 4, n)].copy()
+    blocks = []
+    for period in (1, 1, 2, 3, 4, 6, 7, 8, 12):
+        unit = alpha[rng.integers(0, 4, period)]
+        size = int(rng.integers(150, 400))
+        s = int(rng.integers(0, n - size))
+        g[s:s + size] = np.resize(unit, size)
+        blocks.append((s, size))
+    ref = g.tobytes().decode()
+    reads, es = [], []
+    for _ in range(n_reads):
+        L = int(rng.integers(max(20, mrl // 2), mrl + 1))
+        kind = rng.random()
+        if kind < 0.5:  # from (or across the edge of) a low-complexity block
+            s0, size = blocks[int(rng.integers(0, len(blocks)))]
+            s = int(np.clip(s0 + rng.integers(-L // 2, size), 0, n - L))
+            rd = bytearray(ref[s:s + L].encode())
+            for _k in range(int(rng.integers(0, 3))):
+                rd[int(rng.integers(0, L))] = b"ACGT"[int(rng.integers(0, 4))]
+        elif kind < 0.8:  # a pure tandem repeat, period 1..8
+            unit = alpha[rng.integers(0, 4, int(rng.integers(1, 9)))]
+            rd = bytearray(np.resize(unit, L).tobytes())
+        else:
+            rd = bytearray(alpha[rng.integers(0, 4, L)].tobytes())
+        reads.append(rd.decode())
+        es.append(int(rng.integers(0, 6)))
+    return ref, reads, es, blocks
+
+
+@pytest.mark.parametrize("q", [5, 6])
+def test_repeated_tokens(q):
+    """Reads whose tokens repeat many times (homopolymers, short tandem
+    repeats): the multiplicity planes above the first two -- in shared
+    memory for 128-byte vectors, the list of heavy tokens for 512-byte ones
+    -- in candidate mode and in the coarse-then-exact all-bins mode."""
+    rng = np.random.default_rng(1100 + q)
+    B, mrl = 40, 150
+    ref, reads, e, blocks = _low_complexity_case(rng, 60_000, 400, mrl)
+    rs = Reads(reads, e)
+    idx, oix = _check_tables(_np(ref), B, q, mrl, layouts=7)
+    nb = oix.num_bins
+    block_bins = np.concatenate([np.arange(s // B, min(nb, (s + size) // B + 1))
+                                 for s, size in blocks]).astype(np.int32)
+    lists = []
+    for _ in reads:
+        picks = [rng.integers(0, nb, int(rng.integers(0, 30))),
+                 rng.choice(block_bins, int(rng.integers(0, 30)))]
+        lists.append(np.concatenate(picks).astype(np.int32))
+    off = np.zeros(len(reads) + 1, np.uint64)
+    off[1:] = np.cumsum([len(x) for x in lists])
+    cand = np.concatenate(lists).astype(np.int32)
+    want = oracle.filter(oix, rs, cand_off=off, cand=cand)
+    assert len(want[0]) > 100  # the repeats do pass somewhere
+    assert_same(gpu_filter(idx, rs, off, cand), want)
+    assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
