@@ -27,6 +27,10 @@ MUTANTS = {
                              "sum += tok[j] >= 0 ? vec_bit(v, tok[j]) : 1;"),
     "case_sensitive": ("case 'a': return 0;", "case 'a': return -1;"),
     "bins_floor": ("return B ? (n + B - 1) / B : 0;", "return B ? n / B : 0;"),
+    # a run of one repeated token counted once (a set reading of homopolymers)
+    "repeats_counted_once": ("if (tok[j] >= 0) sum += vec_bit(v, tok[j]);",
+                             "if (tok[j] >= 0 && (j == 0 || tok[j] != tok[j - 1])) "
+                             "sum += vec_bit(v, tok[j]);"),
 }
 
 
@@ -69,6 +73,16 @@ def _pins_hold() -> bool:
         r, b, c = oracle.filter(idx, Reads(rds, es))
         got = list(zip(r.tolist(), b.tolist(), c.tolist()))
         if got != bruteforce.filter(ref, B, mrl - 1, q, rds, es):
+            return False
+    # homopolymer and tandem-repeat reads against a genome holding such runs
+    ref = "ACGTTGCA" * 5 + "A" * 60 + "CACGTCAGGT" * 4 + "AC" * 30 + "TTGACGCATG" * 3
+    rds = ["A" * 30, "AC" * 15, "CA" * 12 + "G", "ACGTTGCA" * 3, "A" * 20 + "CACG"]
+    es = [0, 1, 0, 2, 1]
+    for q, B in ((3, 25), (4, 40)):
+        idx = oracle.bin_vectors(np.frombuffer(ref.encode(), np.uint8), B, q, 40)
+        r, b, c = oracle.filter(idx, Reads(rds, es))
+        got = list(zip(r.tolist(), b.tolist(), c.tolist()))
+        if got != bruteforce.filter(ref, B, 39, q, rds, es):
             return False
     return True
 

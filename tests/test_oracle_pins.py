@@ -99,6 +99,40 @@ def test_bruteforce_random_candidates(seed):
     assert got == want
 
 
+@pytest.mark.parametrize("q", [4, 5, 6])
+def test_bruteforce_repeated_tokens(q):
+    """Homopolymers and short tandem repeats: a read position counts every
+    time its token occurs, so one token can contribute up to L-q+1 to a sum
+    (the multiset reading).  The brute force counts positions by substring
+    search."""
+    rng = np.random.default_rng(3000 + q)
+    alpha = "ACGT"
+    parts = []
+    for _ in range(12):
+        if rng.random() < 0.5:
+            unit = "".join(alpha[i] for i in rng.integers(0, 4, int(rng.integers(1, 8))))
+            parts.append((unit * 80)[: int(rng.integers(30, 90))])
+        else:
+            parts.append("".join(alpha[i] for i in rng.integers(0, 4, int(rng.integers(20, 80)))))
+    ref = "".join(parts)
+    B, mrl = int(rng.integers(20, 50)), 60
+    reads, e = [], []
+    for _ in range(30):
+        L = int(rng.integers(q + 4, mrl + 1))
+        if rng.random() < 0.6:
+            s = int(rng.integers(0, len(ref) - L))
+            reads.append(ref[s:s + L])
+        else:
+            unit = "".join(alpha[i] for i in rng.integers(0, 4, int(rng.integers(1, 4))))
+            reads.append((unit * L)[:L])
+        e.append(int(rng.integers(0, 3)))
+    got = _run_oracle(ref, B, mrl, q, reads, e)
+    assert got == bruteforce.filter(ref, B, mrl - 1, q, reads, e)
+    # some pass counts exceed the number of distinct tokens of their read
+    distinct = {i: len({r[j:j + q] for j in range(len(r) - q + 1)}) for i, r in enumerate(reads)}
+    assert any(c > distinct[r] for r, _, c in got)
+
+
 @pytest.mark.parametrize("q", [3, 4, 5])
 def test_vector_popcount_is_distinct_qgrams(q):
     """Each bin's bits are exactly the distinct clean q-grams of its window."""
