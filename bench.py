@@ -484,6 +484,10 @@ def run_reference(args, rank, world):
         return
     import oracle
 
+    if world > 1:
+        # rank 0 is the only rank at work: give the oracle every host core
+        # (torchrun starts each rank with one OpenMP thread)
+        oracle.set_threads(os.cpu_count() or 1)
     w = workload(args, 0)
     oix = oracle.bin_vectors(w["genome"], w["B"], w["q"], w["max_read_len"])
     rs = w["reads"]

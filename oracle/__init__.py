@@ -75,6 +75,8 @@ def _bind(path) -> C.CDLL:
     lib.oracle_free.restype = None
     lib.oracle_free.argtypes = [C.POINTER(_Out)]
     lib.oracle_threads.restype = C.c_int
+    lib.oracle_set_threads.restype = None
+    lib.oracle_set_threads.argtypes = [C.c_int]
     return lib
 
 
@@ -92,6 +94,11 @@ def _p(a: np.ndarray | None) -> int | None:
 def threads() -> int:
     """OpenMP threads the oracle uses (``OMP_NUM_THREADS`` or all cores)."""
     return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """Run the oracle's parallel loops on ``n`` OpenMP threads."""
+    _load().oracle_set_threads(int(n))
 
 
 def num_bins(n: int, B: int) -> int:

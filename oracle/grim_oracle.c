@@ -247,3 +247,12 @@ int oracle_threads(void) {
   return 1;
 #endif
 }
+
+/* Sets the OpenMP thread count of the oracle's parallel loops (n >= 1). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
