@@ -16,8 +16,9 @@
 //   POPC per 32 bits instead of one bit test per token.
 // * A bin vector (4^q bits) is gathered by G lanes with 16-byte loads
 //   (q = 5: 8 lanes x 16 B = 128 B, four candidates per warp step; q = 6:
-//   32 lanes x 16 B = 512 B); the lane group reduces its partial sums with
-//   shuffles and compares with T = (L-q+1) - q*e.
+//   32 lanes x 16 B = 512 B).  The U vectors of a step are reduced over the
+//   lane group together (a butterfly that halves the sums at each exchange),
+//   compared with T = (L-q+1) - q*e, and one ballot places the passes.
 // * The path is a random 128/512-byte gather per (read, bin) pair: bound by
 //   HBM, not by arithmetic.
 #include "grim_internal.cuh"
