@@ -4,7 +4,7 @@
 //
 // GB300 mapping
 // -------------
-// * A persistent CTA (one per SM, up to 768 threads) takes work items (tile
+// * A persistent CTA (one per SM, up to 640 threads) takes work items (tile
 //   of TW*32 bins, range of reads).  The tile -- 4^q rows x TW words of the
 //   token-major table -- is staged in shared memory once per item and reused
 //   by every read of the range.  TW = 32 (1024 bins, 128 KB at q = 5) up to q = 5 and
@@ -50,7 +50,10 @@
 namespace grim {
 namespace {
 
-constexpr int kMaxThreads = 768;  // 24 warps: 80 registers a thread
+// 20 warps, 96 registers a thread: no spills.  On GB300 this beat 24 warps
+// at 80 registers (which spill a few words) by 4.7% at q = 5 and 2.4% at
+// q = 6; 16, 18 and 28 warps were also slower than 20.
+constexpr int kMaxThreads = 640;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 constexpr uint64_t kRangeTokenBytes = 48ull << 20;  // token rows of one read range: L2-resident
@@ -481,7 +484,8 @@ void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec
   // tiles; kSlotBlocksNarrow for the 256-bin tiles of q = 6, whose 128 KB
   // tile leaves little room for the sixteen groups' slots of a warp -- the
   // later blocks come from L2, and the warps that the smaller slots make
-  // room for hide that latency (1 block: 24 warps per SM; 7 blocks: 11)
+  // room for hide that latency (measured at 768-thread CTAs: 1 block let
+  // 24 warps per SM fit, 7 blocks 11)
   const uint32_t blocks = rv.ts / kBlockTokens;
   a.slot_blocks = ix.r4 <= 1024 ? blocks : min(blocks, kSlotBlocksNarrow);
   a.row_stride = a.slot_blocks * kBlockTokens * 2u;
