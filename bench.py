@@ -43,10 +43,10 @@ METRIC = "reads/s filtered vs whole 3.1 Gbp bin table"
 UNIT = "reads/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
-# launch of the dominant kernel, from a one-pass ncu capture of this
-# benchmark at its default sizes, keyed by the SHA-256 of the kernel source
-# they were taken with and by the workload: a changed kernel, another
-# workload or other sizes report null until measured.
+# launch of a roofline's kernel, from a one-pass ncu capture of this
+# benchmark at its default sizes, keyed by the SHA-256 of the kernel's
+# source file and by the workload: a changed kernel, another workload or
+# other sizes report null until measured.
 TRAFFIC = {
     ("6a9cfdf084e3cc8c", "human"): {"exhaustive_coarse": 6_258_225_920 + 284_662_272},
 }
@@ -55,12 +55,12 @@ TRAFFIC = {
 DEFAULT_GENOME, DEFAULT_READS = 3_100_000_000, 1_000_000
 
 
-def traffic_for(args, dom: str):
+def traffic_for(args, dom: str, source: str = "grim_exhaustive.cu"):
     if args.traffic is not None:
         return args.traffic
     if args.genome != DEFAULT_GENOME or args.reads != DEFAULT_READS:
         return None
-    return TRAFFIC.get((kernel_sha(), args.workload), {}).get(dom)
+    return TRAFFIC.get((kernel_sha(source), args.workload), {}).get(dom)
 
 
 def parse_args():
@@ -92,10 +92,10 @@ def parse_args():
     return p.parse_args()
 
 
-def kernel_sha() -> str:
+def kernel_sha(source: str = "grim_exhaustive.cu") -> str:
     import hashlib
 
-    src = ROOT / "paper_1708_04329_gb300" / "csrc" / "grim_exhaustive.cu"
+    src = ROOT / "paper_1708_04329_gb300" / "csrc" / source
     return hashlib.sha256(src.read_bytes()).hexdigest()[:16]
 
 
@@ -375,7 +375,8 @@ def run_native(args, rank, world, local):
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         leg = {"bound": "hbm", "kernel": "k_candidates", "kernel_ms": k_ms,
                "algorithmic_bytes": round(gbytes * 1e9), "achieved": round(gbytes / (k_ms / 1e3), 1),
-               "peak": hbm, "unit": "GB/s", "frac": round(gbytes / (k_ms / 1e3) / hbm, 4)}
+               "peak": hbm, "unit": "GB/s", "frac": round(gbytes / (k_ms / 1e3) / hbm, 4),
+               "traffic": traffic_for(args, "candidates", "grim_candidates.cu")}
         ceiling = gather_ceiling(nb, vec, n_cand, st)
         if ceiling.get("gbs"):
             ceiling["frac_of_hbm"] = round(ceiling["gbs"] / hbm, 4)
@@ -629,7 +630,8 @@ def run_ragged(args, rank, world, local):
         "roofline": {"bound": "hbm", "kernel": "k_candidates (plain call)",
                      "kernel_ms": round(kernel_ms, 3),
                      "achieved": round(gbytes / (kernel_ms / 1e3), 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(gbytes / (kernel_ms / 1e3) / hbm, 4), "traffic": None,
+                     "frac": round(gbytes / (kernel_ms / 1e3) / hbm, 4),
+                     "traffic": traffic_for(args, "candidates", "grim_candidates.cu"),
                      "algorithmic_bytes": round(gbytes * 1e9)},
     }
     ceiling = gather_ceiling(nb, vec_bytes, n_cand, st)
