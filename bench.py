@@ -49,6 +49,8 @@ UNIT = "reads/s"
 # other sizes report null until measured.
 TRAFFIC = {
     ("6a9cfdf084e3cc8c", "human"): {"exhaustive_coarse": 6_258_225_920 + 284_662_272},
+    ("5e86f343efc540dd", "ragged"): {"candidates": 170_918_996_992 + 255_226_368},
+    ("5e86f343efc540dd", "finer"): {"candidates": 169_915_932_416 + 14_012_416},
 }
 
 
