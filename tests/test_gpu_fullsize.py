@@ -4,8 +4,9 @@ token-major table) and 1,000,000 reads of L=100 with 0-5 edits, e=5, every
 read against every bin in one grim_filter call.
 
 The oracle cannot redo 1.5e15 bit tests, so the GPU's complete output is
-checked on slices the oracle computes exactly -- every bin for a fixed set of
-reads, every read for a fixed range of bins -- plus the bin-major table byte
+checked on slices the oracle computes exactly -- every bin for 128 reads
+spread over the batch, every read for the first and the last 2,048 bins --
+plus the bin-major table byte
 for byte, sampled token-major tiles, and properties that hold at any size.
 """
 import numpy as np
@@ -18,7 +19,7 @@ pytestmark = [pytest.mark.gpu]
 
 torch = pytest.importorskip("torch")
 
-SAMPLE_READS = 32
+SAMPLE_READS = 128
 SAMPLE_BINS = 2048
 
 
@@ -71,11 +72,16 @@ def test_every_bin_for_sampled_reads(human):
         assert np.array_equal(c[sel], want_c[ws]), ridx
 
 
-def test_every_read_for_a_bin_range(human):
+@pytest.mark.parametrize("where", ["first", "last"])
+def test_every_read_for_a_bin_range(human, where):
+    """Every read against the first bins, and against the last ones (the
+    ragged last tile and super-bin of the table)."""
     w, _, got, oix = human
-    want = oracle.filter(oix, w["reads"], bin_range=(0, SAMPLE_BINS))
+    lo = 0 if where == "first" else oix.num_bins - SAMPLE_BINS
+    hi = lo + SAMPLE_BINS
+    want = oracle.filter(oix, w["reads"], bin_range=(lo, hi))
     r, b, c = got
-    sel = b < SAMPLE_BINS
+    sel = (b >= lo) & (b < hi)
     assert np.array_equal(r[sel], want[0])
     assert np.array_equal(b[sel], want[1])
     assert np.array_equal(c[sel], want[2])
