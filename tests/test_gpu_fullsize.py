@@ -6,8 +6,8 @@ read against every bin in one grim_filter call.
 The oracle cannot redo 1.5e15 bit tests, so the GPU's complete output is
 checked on slices the oracle computes exactly -- every bin for 128 reads
 spread over the batch, every read for the first and the last 2,048 bins --
-plus the bin-major table byte
-for byte, sampled token-major tiles, and properties that hold at any size.
+plus the bin-major table byte for byte, sampled token-major tiles, and
+properties that hold at any size.
 """
 import numpy as np
 import pytest
