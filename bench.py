@@ -48,7 +48,7 @@ UNIT = "reads/s"
 # source file and by the workload: a changed kernel, another workload or
 # other sizes report null until measured.
 TRAFFIC = {
-    ("6a9cfdf084e3cc8c", "human"): {"exhaustive_coarse": 6_258_225_920 + 284_662_272},
+    ("9175c34e74cb0b6f", "human"): {"exhaustive_coarse": 6_697_551_360 + 280_390_400},
     ("5e86f343efc540dd", "ragged"): {"candidates": 170_918_996_992 + 255_226_368},
     ("5e86f343efc540dd", "finer"): {"candidates": 169_915_932_416 + 14_012_416},
 }
@@ -57,12 +57,17 @@ TRAFFIC = {
 DEFAULT_GENOME, DEFAULT_READS = 3_100_000_000, 1_000_000
 
 
-def traffic_for(args, dom: str, source: str = "grim_exhaustive.cu"):
+# the all-bins kernel's traffic also depends on the token order the
+# tokeniser writes, so its key covers both sources
+EXHAUSTIVE_SOURCES = ("grim_exhaustive.cu", "grim_tokens.cu")
+
+
+def traffic_for(args, dom: str, sources=EXHAUSTIVE_SOURCES):
     if args.traffic is not None:
         return args.traffic
     if args.genome != DEFAULT_GENOME or args.reads != DEFAULT_READS:
         return None
-    return TRAFFIC.get((kernel_sha(source), args.workload), {}).get(dom)
+    return TRAFFIC.get((kernel_sha(sources), args.workload), {}).get(dom)
 
 
 def parse_args():
@@ -94,11 +99,15 @@ def parse_args():
     return p.parse_args()
 
 
-def kernel_sha(source: str = "grim_exhaustive.cu") -> str:
+def kernel_sha(sources=EXHAUSTIVE_SOURCES) -> str:
     import hashlib
 
-    src = ROOT / "paper_1708_04329_gb300" / "csrc" / source
-    return hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    if isinstance(sources, str):
+        sources = (sources,)
+    h = hashlib.sha256()
+    for name in sources:
+        h.update((ROOT / "paper_1708_04329_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
 
 
 def dist_env():
