@@ -194,6 +194,36 @@ def test_qgram_lemma_true_bin_passes(tiny_plain, tiny_plain_oracle):
         assert (i, int(rs.true_pos[i]) // B) in got
 
 
+@pytest.mark.parametrize("q,B,lengths,e_fixed", [
+    (6, 100, (150,), 7),              # the finer index: T = 145 - 42 = 103
+    (5, 200, (100, 150, 250), None),  # mixed lengths, e up to 0.05 L, ext = 249
+])
+def test_qgram_lemma_other_configurations(q, B, lengths, e_fixed):
+    """The same lemma at the other index shapes: q = 6 with B = 100, and
+    reads of 100-250 bp with per-read budgets against an index extended by
+    249 bases.  Reads are planted with up to e edits (substitutions,
+    insertions, deletions) on a repeat-rich genome; every true bin passes,
+    and edit-free reads count all L-q+1 tokens there."""
+    from paper_1708_04329_gb300 import synth
+
+    g = synth.human_genome(300_000, seed=12)
+    mrl = max(lengths)
+    if e_fixed is None:
+        rs = synth.reads(g, 400, seed=13, lengths=lengths, probs=(0.5, 0.3, 0.2), e_frac=(5, 100),
+                         max_edits=None)
+    else:
+        rs = synth.reads(g, 400, seed=13, lengths=lengths, e=e_fixed, max_edits=e_fixed)
+    idx = oracle.bin_vectors(g, B, q, mrl)
+    true_bin = (rs.true_pos // B).astype(np.int32)
+    off = np.arange(rs.n + 1, dtype=np.uint64)
+    r, b, c = oracle.filter(idx, rs, cand_off=off, cand=true_bin)
+    assert (rs.n_edits <= rs.e).all()
+    assert r.tolist() == list(range(rs.n))  # every read passes its true bin
+    exact = rs.n_edits == 0
+    assert exact.sum() > 20
+    assert (c[exact] == rs.lens[exact] - q + 1).all()
+
+
 def test_exact_reads_full_count(tiny_plain, tiny_plain_oracle):
     """Reads with 0 edits find all L-q+1 tokens in their true bin."""
     rs = tiny_plain["reads"]
