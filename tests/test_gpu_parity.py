@@ -385,3 +385,23 @@ def test_repeated_tokens(q):
     assert len(want[0]) > 100  # the repeats do pass somewhere
     assert_same(gpu_filter(idx, rs, off, cand), want)
     assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
+
+
+@pytest.mark.parametrize("layouts", [1, 6, 7])
+def test_degenerate_genome_and_reads(layouts):
+    """A genome of non-bases (no bin holds any q-gram: only reads with T <= 0
+    pass, with count 0) and a read of non-bases against a clean genome, in
+    the all-bins paths and in candidate mode."""
+    q, B, mrl = 4, 10, 20
+    reads = ["ACGTACGTAC", "NNNNNNNNNN", "ACGTNACGTA", "acgtacgtac", "NNNNNNNNNNNNNNNNNNNN"]
+    for ref, e in (("N" * 2_095, [0, 2, 2, 3, 5]), ("ACGTTGCAAC" * 300, [1, 2, 0, 1, 5]),
+                   ("ACGTTGCAAC" * 300, [0, 1, 1, 0, 4])):
+        rs = Reads(reads, e)
+        idx, oix = _check_tables(_np(ref), B, q, mrl, layouts)
+        assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
+        if layouts & 2:
+            nb = oix.num_bins
+            off = np.array([0, 3, 3, 7, 9, 12], np.uint64)
+            cand = np.array([0, 1, nb - 1, 5, 4, 3, 2, 0, nb - 1, 7, 8, 9], np.int32)
+            assert_same(gpu_filter(idx, rs, off, cand), oracle.filter(oix, rs, cand_off=off, cand=cand))
+        idx.close()

@@ -285,6 +285,36 @@ def test_alphabet_relabelling_invariant():
     assert a == b and len(a) > 0
 
 
+def test_degenerate_genomes_and_reads():
+    """Degenerate inputs against the brute force and the plain facts they
+    imply: a genome of non-bases has no q-gram in any bin, so only reads
+    whose threshold is <= 0 pass, with count 0; a genome shorter than q is
+    one bin with an empty vector; a read of non-bases only counts nothing
+    anywhere but still has L-q+1 tokens (it passes only when q*e >= L-q+1)."""
+    q, B, mrl = 4, 10, 20
+    reads = ["ACGTACGTAC", "NNNNNNNNNN", "ACGTNACGTA", "acgtacgtac"]
+    # all non-bases
+    ref = "N" * 95
+    for e in ([0, 0, 0, 0], [2, 2, 2, 2], [3, 1, 2, 3]):
+        got = _run_oracle(ref, B, mrl, q, reads, e)
+        assert got == bruteforce.filter(ref, B, mrl - 1, q, reads, e)
+        for r, _, c in got:
+            assert c == 0 and (len(reads[r]) - q + 1) - q * e[r] <= 0
+        nb = -(-len(ref) // B)
+        passing = [i for i in range(len(reads)) if (len(reads[i]) - q + 1) - q * e[i] <= 0]
+        assert sorted({r for r, _, _ in got}) == passing
+        assert len(got) == nb * len(passing)
+    # shorter than q: one bin, nothing in it
+    idx = oracle.bin_vectors(np.frombuffer(b"ACG", dtype=np.uint8), B, q, mrl)
+    assert idx.num_bins == 1 and not idx.vecs.any()
+    # a read of non-bases against a clean genome
+    ref = "ACGTTGCAAC" * 12
+    for e in (1, 2):
+        got = _run_oracle(ref, B, mrl, q, ["NNNNNNNNNN"], [e])
+        assert got == bruteforce.filter(ref, B, mrl - 1, q, ["NNNNNNNNNN"], [e])
+        assert bool(got) == (q * e >= 10 - q + 1)
+
+
 def test_errors():
     idx = oracle.bin_vectors(np.frombuffer(b"ACGTACGTAC", dtype=np.uint8), 4, 3, 6)
     with pytest.raises(oracle.OracleError) as ei:
