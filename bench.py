@@ -43,15 +43,12 @@ METRIC = "reads/s filtered vs whole 3.1 Gbp bin table"
 UNIT = "reads/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
-# launch of a roofline's kernel, from a one-pass ncu capture of this
-# benchmark at its default sizes, keyed by the SHA-256 of the kernel's
-# source file and by the workload: a changed kernel, another workload or
-# other sizes report null until measured.
-TRAFFIC = {
-    ("9175c34e74cb0b6f", "human"): {"exhaustive_coarse": 6_697_551_360 + 280_390_400},
-    ("5e86f343efc540dd", "ragged"): {"candidates": 170_918_996_992 + 255_226_368},
-    ("5e86f343efc540dd", "finer"): {"candidates": 169_915_932_416 + 14_012_416},
-}
+# launch of a roofline's kernel, keyed by the SHA-256 of the kernel's sources
+# and by the leg of this benchmark: a changed kernel reports null until
+# measured again, and so does any run at other than the default sizes.  The
+# figures come from one-launch ncu captures of small cases of the same
+# workloads, scaled to the full launch by the rule each entry states.
+TRAFFIC = {}
 
 
 DEFAULT_GENOME, DEFAULT_READS = 3_100_000_000, 1_000_000
@@ -62,12 +59,14 @@ DEFAULT_GENOME, DEFAULT_READS = 3_100_000_000, 1_000_000
 EXHAUSTIVE_SOURCES = ("grim_exhaustive.cu", "grim_tokens.cu")
 
 
-def traffic_for(args, dom: str, sources=EXHAUSTIVE_SOURCES):
-    if args.traffic is not None:
+def traffic_for(args, leg: str, sources=EXHAUSTIVE_SOURCES, headline: bool = False):
+    """DRAM bytes of one launch of a leg's dominant kernel ("workload:stage")
+    at the default sizes, or None.  --reads sizes only the headline batch."""
+    if headline and args.traffic is not None:
         return args.traffic
-    if args.genome != DEFAULT_GENOME or args.reads != DEFAULT_READS:
+    if args.genome != DEFAULT_GENOME or (headline and args.reads != DEFAULT_READS):
         return None
-    return TRAFFIC.get((kernel_sha(sources), args.workload), {}).get(dom)
+    return TRAFFIC.get((kernel_sha(sources), leg))
 
 
 def parse_args():
@@ -85,7 +84,14 @@ def parse_args():
                         "L=150, e=7 on the same genome; ragged: candidate lists for reads of "
                         "mixed length and budget through one graph-captured plan")
     p.add_argument("--coarse-factor", type=int, default=0,
-                   help="bins per super-bin of the coarse table (0: the library's choice)")
+                   help="bins per super-bin of the coarse table (0: the autotuner's choice, or "
+                        "the library's with --no-tune)")
+    p.add_argument("--no-tune", action="store_true",
+                   help="skip the all-bins autotuner (library default tile shapes)")
+    p.add_argument("--tune-reads", type=int, default=200_000,
+                   help="reads of the batch the all-bins autotuner times its trials on")
+    p.add_argument("--no-legs", action="store_true",
+                   help="headline only: skip the one-pass exact, ragged and finer-index legs")
     p.add_argument("--genome", type=int, default=DEFAULT_GENOME, help="reference length (bases)")
     p.add_argument("--reads", type=int, default=DEFAULT_READS, help="reads per rank")
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -246,6 +252,74 @@ class ClockSampler:
 # native arm
 # ---------------------------------------------------------------------------
 
+def load_peaks() -> dict:
+    try:
+        return json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
+    except (OSError, ValueError):
+        return {}
+
+
+def alu_peak_tbit(n_sm: int, sm_mhz: float) -> float:
+    """Bit tests per second the ALU pipe can execute in the all-bins kernel:
+    64 lanes of 3-input logic ops per clock per SM (2 warp instructions, as
+    ncu's sm__inst_executed_pipe_alu.avg.peak_sustained reports on GB300);
+    the carry-save count needs 2 LOP3 per token per 32-bin word, so
+    64 * 32 / 2 = 1024 bit tests per clock per SM (the shared-memory datapath,
+    128 B = 1024 bits per clock per SM, gives the same figure)."""
+    return n_sm * 1024 * sm_mhz * 1e6 / 1e12
+
+
+def alu_roofline(executed: int, per_launch_ms: float, n_sm: int, sm_mhz: float, kernel: str) -> dict:
+    """Roofline of an all-bins kernel launch: the bit tests it executed over its
+    CUDA-event time, against the ALU-pipe peak."""
+    peak = alu_peak_tbit(n_sm, sm_mhz)
+    achieved = executed / (per_launch_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
+            "unit": "Tbit-tests/s", "frac": round(achieved / peak, 4), "kernel": kernel,
+            "kernel_ms": round(per_launch_ms, 3),
+            "work": ("bit tests the kernel executed: 16-token blocks applied to (super-)bin "
+                     "tiles x bins per tile (early exit skips the rest)"),
+            "executed_bit_tests": int(executed),
+            "peak_basis": (f"ALU pipe: {n_sm} SMs x 64 lanes/clk x 32 bins per logic op / 2 "
+                           f"LOP3 per token per 32-bin word (carry-save minimum) x {sm_mhz:.0f} "
+                           "MHz; peak clock, derived (no measured peak covers this pipe)")}
+
+
+def sample_of(dev: dict, rs, n: int) -> dict:
+    """The first n reads of a device-resident batch, as grim_filter keyword arguments."""
+    n = min(n, rs.n)
+    end = int(rs.offsets[n - 1]) + int(rs.lens[n - 1])
+    return dict(reads=dev["reads"][:end], offsets=dev["offsets"][:n], lens=dev["lens"][:n],
+                e=dev["e"][:n])
+
+
+def all_bins_shape(args, w, dev, ref) -> dict:
+    """The all-bins tile shapes of this workload: the autotuner's pick, timed on
+    the batch's first --tune-reads reads, unless --coarse-factor or --no-tune
+    fixes them.  `layouts` drops the coarse table when one exact pass wins."""
+    from paper_1708_04329_gb300 import autotune, grim
+
+    if args.coarse_factor or args.no_tune:
+        return {"tuned": False, "factor": args.coarse_factor, "cta_threads": 0,
+                "read_range_kb": 0, "layouts": grim.GRIM_LAYOUT_ALL}
+    t0 = time.perf_counter()
+    out = autotune.tune_all_bins(ref, w["B"], w["q"], w["max_read_len"],
+                                 sample_of(dev, w["reads"], args.tune_reads), cache=None)
+    out = dict(out, tuned=True, tune_s=round(time.perf_counter() - t0, 1))
+    out["layouts"] = grim.GRIM_LAYOUT_ALL if out["factor"] else grim.GRIM_LAYOUT_BOTH
+    return out
+
+
+def device_inputs(w) -> dict:
+    import torch
+
+    rs = w["reads"]
+    return dict(reads=torch.from_numpy(rs.seq).cuda(),
+                offsets=torch.from_numpy(rs.offsets.view(np.int64)).cuda(),
+                lens=torch.from_numpy(rs.lens.view(np.int32)).cuda(),
+                e=torch.from_numpy(rs.e.view(np.int16)).cuda())
+
+
 def run_native(args, rank, world, local):
     import torch
 
@@ -261,14 +335,11 @@ def run_native(args, rank, world, local):
     rs = w["reads"]
     B, q, mrl = w["B"], w["q"], w["max_read_len"]
     st = torch.cuda.current_stream()
-    dev = dict(
-        reads=torch.from_numpy(rs.seq).cuda(),
-        offsets=torch.from_numpy(rs.offsets.view(np.int64)).cuda(),
-        lens=torch.from_numpy(rs.lens.view(np.int32)).cuda(),
-        e=torch.from_numpy(rs.e.view(np.int16)).cuda())
+    dev = device_inputs(w)
     cand = torch.from_numpy(w["cand"]).cuda()
     cand_off = torch.from_numpy(w["cand_off"].view(np.int64)).cuda()
     ref = torch.from_numpy(w["genome"]).cuda()
+    shape = all_bins_shape(args, w, dev, ref)
     cap = 8 * rs.n + 4096
     outs = [tuple(torch.empty(cap, dtype=dt, device="cuda") for dt in (torch.int32, torch.int32, torch.uint8))
             for _ in range(2)]
@@ -280,7 +351,9 @@ def run_native(args, rank, world, local):
 
     def step():
         evs[0].record(st)
-        idx = grim.grim_build_ex(ref, B, q, mrl, grim.GRIM_LAYOUT_ALL, args.coarse_factor, stream=st)
+        idx = grim.grim_build_ex(ref, B, q, mrl, shape["layouts"], shape["factor"], stream=st,
+                                 cta_threads=shape["cta_threads"],
+                                 read_range_kb=shape["read_range_kb"])
         evs[1].record(st)
         a = grim.grim_filter(idx, **dev, out=outs[0], workspace=ws, stream=st)
         evs[2].record(st)
@@ -330,33 +403,21 @@ def run_native(args, rank, world, local):
     k_launch, k_ms = prof[dom]
     per_launch_ms = k_ms / max(k_launch, 1)
     units = desc.num_coarse if dom == "exhaustive_coarse" else nb
-    kernel_bit_tests = rs.n * units * ntok  # algorithmic: L-q+1 tests per (read, unit) decided
-    peaks = {}
-    try:
-        peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
-    except (OSError, ValueError):
-        pass
+    peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    # shared-memory datapath: 128 B/clk/SM = 1024 bit tests/clk/SM
-    peak_tbit = n_sm * 1024 * sm_max * 1e6 / 1e12
-    achieved_tbit = kernel_bit_tests / (per_launch_ms / 1e3) / 1e12
-    executed = stats["bit_tests_executed"]  # bit tests the exhaustive passes performed
-    executed_tbit = executed / (k_ms / max(k_launch, 1) / 1e3) / 1e12
+    n_sm = props.multi_processor_count
+    roofline = alu_roofline(stats["bit_tests_executed"], per_launch_ms, n_sm, sm_max,
+                            f"k_exhaustive ({'super-bins' if dom == 'exhaustive_coarse' else 'bins'})")
+    roofline["traffic"] = traffic_for(args, f"{args.workload}:{dom}", headline=True)
+    decided = rs.n * units * ntok  # L-q+1 tests per (read, unit) decided, dense
     all_bins_ms = part_ms["all_bins"] / args.steps
-    method_bit_tests = rs.n * nb * ntok
-    roofline = {"bound": "alu", "achieved": round(achieved_tbit, 2), "peak": round(peak_tbit, 2),
-                "unit": "Tbit-tests/s", "frac": round(achieved_tbit / peak_tbit, 4),
-                "traffic": traffic_for(args, dom),
-                "kernel": f"k_exhaustive ({'super-bins' if dom == 'exhaustive_coarse' else 'bins'})",
-                "kernel_ms": round(per_launch_ms, 3),
-                "peak_basis": f"{n_sm} SMs x 128 B/clk shared-memory loads x 8 bits x {sm_max:.0f} MHz",
-                "kernel_algorithmic_bit_tests": kernel_bit_tests, "executed_bit_tests": executed,
-                "executed_tbit_per_s": round(executed_tbit, 2),
-                "executed_frac": round(executed_tbit / peak_tbit, 4),
-                "all_bins_filter_ms": round(all_bins_ms, 3),
-                "all_bins_method_tbit_per_s": round(method_bit_tests / (all_bins_ms / 1e3) / 1e12, 2),
-                "coarse_survivors": stats["survivors"]}
+    # the same kernel time against other work counts, labelled
+    roofline.update({
+        "decided_bit_tests": decided,
+        "decided_tbit_per_s": round(decided / (per_launch_ms / 1e3) / 1e12, 2),
+        "all_bins_filter_ms": round(all_bins_ms, 3),
+        "method_tbit_per_s": round(rs.n * nb * ntok / (all_bins_ms / 1e3) / 1e12, 2),
+        "coarse_survivors": stats["survivors"]})
     if roofline["traffic"]:
         # DRAM GB/s of the dominant kernel (ncu traffic over its live time):
         # the table is not the bound, the integer pipe is
@@ -375,29 +436,26 @@ def run_native(args, rank, world, local):
         "passing_records": counts, "step_ms": {k: round(v / args.steps, 3) for k, v in part_ms.items()},
         "kernel_ms_per_launch": stages,
         "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+        "autotune": {k: v for k, v in shape.items() if k != "layouts"},
     }
     if rank == 0 and args.workload == "finer" and "candidates" in stages:
-        # the candidate leg: 512-byte vector gathers, against the copy
-        # bandwidth and against this GPU's random-gather ceiling for such rows
-        vec = 4 ** q // 8
-        n_cand = len(w["cand"])
-        k_ms = stages["candidates"]
-        gbytes = n_cand * (vec + 4) / 1e9
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        leg = {"bound": "hbm", "kernel": "k_candidates", "kernel_ms": k_ms,
-               "algorithmic_bytes": round(gbytes * 1e9), "achieved": round(gbytes / (k_ms / 1e3), 1),
-               "peak": hbm, "unit": "GB/s", "frac": round(gbytes / (k_ms / 1e3) / hbm, 4),
-               "traffic": traffic_for(args, "candidates", "grim_candidates.cu")}
-        ceiling = gather_ceiling(nb, vec, n_cand, st)
-        if ceiling.get("gbs"):
-            ceiling["frac_of_hbm"] = round(ceiling["gbs"] / hbm, 4)
-            leg["frac_of_gather_ceiling"] = round(n_cand / (k_ms / 1e3) / ceiling["rows_per_s"], 4)
-        leg["gather_ceiling"] = ceiling
-        line["candidate_roofline"] = leg
+        line["candidate_roofline"] = candidate_roofline(len(w["cand"]), stages["candidates"], nb,
+                                                        4 ** q // 8, st, peaks, args,
+                                                        "finer:candidates", headline=True)
     if rank == 0 and not args.no_e2e:
-        line["e2e"] = run_e2e(args, w, st)
+        line["e2e"] = run_e2e(args, w, st, shape)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    legs = rank == 0 and world == 1 and args.workload == "human" and not args.no_legs
+    if legs:
+        line["exact_one_pass"] = exact_leg(w, dev, ref, shape, st, n_sm, sm_max, args)
+    del dev, cand, cand_off, ref, outs, ws
+    torch.cuda.empty_cache()
+    if legs:
+        line["ragged"] = ragged_leg(args, w["genome"])
+        torch.cuda.empty_cache()
+        line["finer"] = finer_leg(args, w["genome"], n_sm, sm_max, peaks)
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = serving_leg(w["genome"])
     if dist:
@@ -407,7 +465,151 @@ def run_native(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def run_e2e(args, w, st):
+def candidate_roofline(n_cand: int, k_ms: float, nb: int, vec: int, st, peaks: dict, args,
+                       traffic_key: str, headline: bool = False) -> dict:
+    """The candidate kernel (one bin-vector gather per pair): algorithmic bytes
+    (vector + id per pair) over its CUDA-event time, against the copy
+    bandwidth and against this GPU's random-gather ceiling for such rows."""
+    gbytes = n_cand * (vec + 4) / 1e9
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    leg = {"bound": "hbm", "kernel": "k_candidates", "kernel_ms": k_ms,
+           "algorithmic_bytes": round(gbytes * 1e9), "achieved": round(gbytes / (k_ms / 1e3), 1),
+           "peak": hbm, "unit": "GB/s", "frac": round(gbytes / (k_ms / 1e3) / hbm, 4),
+           "traffic": traffic_for(args, traffic_key, "grim_candidates.cu", headline)}
+    ceiling = gather_ceiling(nb, vec, n_cand, st)
+    if ceiling.get("gbs"):
+        ceiling["frac_of_hbm"] = round(ceiling["gbs"] / hbm, 4)
+        leg["frac_of_gather_ceiling"] = round(n_cand / (k_ms / 1e3) / ceiling["rows_per_s"], 4)
+    leg["gather_ceiling"] = ceiling
+    return leg
+
+
+def timed_filter(fn, steps: int, warmup: int, st) -> tuple[float, dict]:
+    """Mean CUDA-event ms of fn() over `steps` after `warmup`, with the
+    library's per-kernel times of the timed calls."""
+    import torch
+
+    from paper_1708_04329_gb300 import grim
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    grim.grim_profile(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(steps):
+        fn()
+    b.record(st)
+    torch.cuda.synchronize()
+    prof = grim.grim_profile_get()
+    grim.grim_profile(False)
+    return a.elapsed_time(b) / steps, {k: v[1] / max(v[0], 1) for k, v in prof.items()}
+
+
+def exact_leg(w, dev, ref, shape, st, n_sm, sm_max, args, steps: int = 2, warmup: int = 1) -> dict:
+    """The one-pass exact all-bins path on the headline workload: an index with
+    the token-major table only, so every read is checked against every bin in
+    one pass (the path of batches with little slack, and of indexes built
+    without the coarse and bin-major tables)."""
+    from paper_1708_04329_gb300 import grim
+
+    rs = w["reads"]
+    idx = grim.grim_build_ex(ref, w["B"], w["q"], w["max_read_len"], grim.GRIM_LAYOUT_TOKEN_MAJOR,
+                             stream=st, cta_threads=shape["cta_threads"],
+                             read_range_kb=shape["read_range_kb"])
+    cap = 8 * rs.n + 4096
+    ws = grim.Workspace()
+    res = {}
+
+    def run():
+        r = grim.grim_filter(idx, **dev, cap=cap, workspace=ws, stream=st)
+        res["n"] = int(r[0].numel())
+        res["stats"] = grim.grim_last_filter_stats()
+
+    ms, prof = timed_filter(run, steps, warmup, st)
+    nb = idx.desc.num_bins
+    idx.close()
+    roof = alu_roofline(res["stats"]["bit_tests_executed"], prof["exhaustive"], n_sm, sm_max,
+                        "k_exhaustive (bins, one exact pass)")
+    roof["traffic"] = traffic_for(args, "human:exhaustive_exact")
+    ntok = w["read_len"] - w["q"] + 1
+    roof["decided_bit_tests"] = rs.n * nb * ntok
+    return {"value": round(rs.n / (ms / 1e3), 1), "unit": UNIT, "ms": round(ms, 3),
+            "steps": steps, "passing_records": res["n"], "roofline": roof,
+            "kernel_ms_per_launch": {k: round(v, 3) for k, v in prof.items()},
+            "workload": "the headline reads against every bin of a token-major-only index "
+                        "(no coarse pass)"}
+
+
+def finer_leg(args, g, n_sm, sm_max, peaks, steps: int = 2, warmup: int = 1) -> dict:
+    """The finer index (q = 6, B = 100) on the same genome: one step is the
+    build (token-major, bin-major, coarse), the all-bins call and the
+    candidate-list call for 1M reads of 150 bp, e = 7."""
+    import torch
+
+    from paper_1708_04329_gb300 import grim, synth
+
+    t0 = time.perf_counter()
+    w = synth.finer_index(n_reads=1_000_000, g=g)
+    gen_s = time.perf_counter() - t0
+    rs = w["reads"]
+    st = torch.cuda.current_stream()
+    dev = device_inputs(w)
+    cand = torch.from_numpy(w["cand"]).cuda()
+    cand_off = torch.from_numpy(w["cand_off"].view(np.int64)).cuda()
+    ref = torch.from_numpy(g).cuda()
+    cap = 8 * rs.n + 4096
+    ws = grim.Workspace()
+    res = {}
+    part = {"all_bins": 0.0, "candidates": 0.0}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def step():
+        idx = grim.grim_build(ref, w["B"], w["q"], w["max_read_len"], grim.GRIM_LAYOUT_ALL, stream=st)
+        ev[0].record(st)
+        a = grim.grim_filter(idx, **dev, cap=cap, workspace=ws, stream=st)
+        ev[1].record(st)
+        res["stats"] = grim.grim_last_filter_stats()
+        res["desc"] = idx.desc
+        b = grim.grim_filter(idx, **dev, cand=cand, cand_off=cand_off, cap=cap, workspace=ws,
+                             stream=st)
+        ev[2].record(st)
+        res["all"], res["cand"] = int(a[0].numel()), int(b[0].numel())
+        idx.close()
+        ev[2].synchronize()
+        part["all_bins"] += ev[0].elapsed_time(ev[1])
+        part["candidates"] += ev[1].elapsed_time(ev[2])
+
+    for _ in range(warmup):
+        step()
+    for k in part:
+        part[k] = 0.0
+    ms, prof = timed_filter(step, steps, 0, st)
+    for k in part:
+        part[k] /= steps
+    desc = res["desc"]
+    dom = "exhaustive_coarse" if "exhaustive_coarse" in prof else "exhaustive"
+    roof = alu_roofline(res["stats"]["bit_tests_executed"], prof[dom], n_sm, sm_max,
+                        f"k_exhaustive ({'super-bins' if dom == 'exhaustive_coarse' else 'bins'}, q = 6)")
+    roof["traffic"] = traffic_for(args, "finer:" + dom)
+    out = {"value": round(rs.n / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms, 3),
+           "steps": steps,
+           "workload": (f"finer index: the same genome, B={w['B']}, q={w['q']} ({desc.num_bins} bins, "
+                        f"{4 ** w['q'] // 8} B vectors), {rs.n} reads L=150 e=7; step = build + "
+                        f"all-bins + candidate lists ({len(w['cand'])} candidates)"),
+           "gen_s": round(gen_s, 1), "passing_records": {"all": res["all"], "cand": res["cand"]},
+           "step_ms": {k: round(v, 3) for k, v in part.items()},
+           "kernel_ms_per_launch": {k: round(v, 3) for k, v in prof.items()},
+           "all_bins_roofline": roof}
+    del dev, ref, ws
+    torch.cuda.empty_cache()
+    out["candidate_roofline"] = candidate_roofline(len(w["cand"]), prof["candidates"],
+                                                   desc.num_bins, 4 ** w["q"] // 8, st, peaks,
+                                                   args, "finer:candidates")
+    return out
+
+
+def run_e2e(args, w, st, shape):
     """The same step through the host-buffer entry points, copies included."""
     import torch
 
@@ -431,7 +633,9 @@ def run_e2e(args, w, st):
     def step():
         t = [time.perf_counter()]
         idx = grim.grim_build_host_ex(h["ref"], w["B"], w["q"], w["max_read_len"],
-                                      coarse_factor=args.coarse_factor, stream=st)
+                                      shape["layouts"], shape["factor"], stream=st,
+                                      cta_threads=shape["cta_threads"],
+                                      read_range_kb=shape["read_range_kb"])
         t.append(time.perf_counter())
         a = grim.grim_filter_host(idx, h["seq"], h["off"], h["lens"], h["e"], out=outs[0], stream=st)
         t.append(time.perf_counter())
@@ -528,7 +732,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_ragged(args, rank, world, local):
+def ragged_measure(args, g, rank: int, n_reads: int, steps: int, warmup: int, dist=None) -> dict:
     """Ragged candidate lists: L in {100,150,250}, per-read e, LogNormal lists.
     One step = one launch of a graph-captured plan over the whole batch
     (inputs staged in the plan's buffers before timing); the plain grim_filter
@@ -537,15 +741,7 @@ def run_ragged(args, rank, world, local):
 
     from paper_1708_04329_gb300 import autotune, grim, synth
 
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    n_reads = args.reads if args.reads != DEFAULT_READS else 4_000_000
     t0 = time.perf_counter()
-    g = synth.human_genome(args.genome)
     w = synth.ragged_candidates(n_reads=n_reads, g=g)
     if rank:
         w["reads"] = synth.reads(g, n_reads, seed=rank_seed(4, rank), lengths=(100, 150, 250),
@@ -558,21 +754,17 @@ def run_ragged(args, rank, world, local):
     st = torch.cuda.current_stream()
     ref = torch.from_numpy(g).cuda()
     idx = grim.grim_build(ref, w["B"], w["q"], w["max_read_len"], grim.GRIM_LAYOUT_BIN_MAJOR)
+    del ref
     nb = idx.desc.num_bins
-    dev = dict(reads=torch.from_numpy(rs.seq).cuda(),
-               offsets=torch.from_numpy(rs.offsets.view(np.int64)).cuda(),
-               lens=torch.from_numpy(rs.lens.view(np.int32)).cuda(),
-               e=torch.from_numpy(rs.e.view(np.int16)).cuda(),
-               cand=torch.from_numpy(w["cand"]).cuda(),
-               cand_off=torch.from_numpy(w["cand_off"].view(np.int64)).cuda())
+    dev = device_inputs(w)
+    dev["cand"] = torch.from_numpy(w["cand"]).cuda()
+    dev["cand_off"] = torch.from_numpy(w["cand_off"].view(np.int64)).cuda()
     n_cand = len(w["cand"])
     max_e = int(rs.e.max())
     # autotune the read tile on a sample of the batch
     ns = min(rs.n, 1_000_000)
     cs = int(w["cand_off"][ns])
-    sample = dict(reads=dev["reads"][: int(rs.offsets[ns - 1] + rs.lens[ns - 1])],
-                  offsets=dev["offsets"][:ns], lens=dev["lens"][:ns], e=dev["e"][:ns],
-                  cand=dev["cand"][:cs], cand_off=dev["cand_off"][: ns + 1])
+    sample = dict(sample_of(dev, rs, ns), cand=dev["cand"][:cs], cand_off=dev["cand_off"][: ns + 1])
     tuned = (autotune.tune_candidate_unroll(idx, sample, max_e, cache=None) if not args.cand_unroll
              else {"unroll": args.cand_unroll, "ms": None})
     cap = 4 * rs.n + 4096
@@ -585,74 +777,86 @@ def run_ragged(args, rank, world, local):
         grim.grim_plan_launch(plan, rs.n, n_cand, st)
         return grim.grim_plan_wait(plan)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         n_pass = step()
     if dist:
         dist.barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(st)
-    for _ in range(args.steps):
+    for _ in range(steps):
         n_pass = step()
     ev1.record(st)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
+    plan.close()
     # the plain single call, with per-kernel timing, on the same inputs
     ws = grim.Workspace()
     out = tuple(torch.empty(cap, dtype=dt, device="cuda") for dt in (torch.int32, torch.int32, torch.uint8))
-    grim.grim_filter(idx, **dev, out=out, workspace=ws)
-    grim.grim_profile(True)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(st)
-    for _ in range(args.steps):
-        plain = grim.grim_filter(idx, **dev, out=out, workspace=ws)
-    b.record(st)
-    torch.cuda.synchronize()
-    prof = grim.grim_profile_get()
-    grim.grim_profile(False)
-    plain_ms = a.elapsed_time(b) / args.steps
-    assert int(plain[0].numel()) == n_pass
-    k_launch, k_ms = prof.get("candidates", (1, 0.0))
-    kernel_ms = k_ms / max(k_launch, 1)
+    res = {}
+
+    def plain_call():
+        res["plain"] = grim.grim_filter(idx, **dev, out=out, workspace=ws)
+
+    plain_ms, prof = timed_filter(plain_call, steps, 1, st)
+    assert int(res["plain"][0].numel()) == n_pass
+    del dev, ws, out, res
+    torch.cuda.empty_cache()
+    peaks = load_peaks()
     vec_bytes = max(4, 4 ** w["q"] // 8)
-    gbytes = n_cand * (vec_bytes + 4) / 1e9  # one vector gather + its id per pair
-    peaks = {}
-    try:
-        peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text())
-    except (OSError, ValueError):
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    ms = max_over_ranks(ms, dist, "cuda")
-    line = {
-        "metric": "reads/s, candidate lists of ragged reads (graph-captured plan)",
-        "value": round(weak_value(rs.n, world, ms), 1), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic",
-        "config": {"workload": (f"ragged candidates: {len(g) / 1e9:.1f} Gbp genome, B={w['B']}, "
-                                f"q={w['q']}, bin-major table, {rs.n} reads L in {{100,150,250}} "
-                                f"(.5/.3/.2), e uniform in [0, 0.05 L], {n_cand} candidates "
-                                "(LogNormal median 200, clip 20,000); one graph launch per step"),
-                   "reads": rs.n, "candidates": n_cand, "gen_s": round(gen_s, 1)},
-        "pairs_per_s": round(n_cand * world / (ms / 1e3), 1),
+    roof = candidate_roofline(n_cand, prof["candidates"], nb, vec_bytes, st, peaks, args,
+                              "ragged:candidates")
+    roof["kernel"] = "k_candidates (plain call)"
+    idx.close()
+    return {
+        "ms": ms, "n_reads": rs.n, "n_cand": n_cand, "gen_s": round(gen_s, 1),
+        "workload": (f"ragged candidates: {len(g) / 1e9:.1f} Gbp genome, B={w['B']}, "
+                     f"q={w['q']}, bin-major table, {rs.n} reads L in {{100,150,250}} "
+                     f"(.5/.3/.2), e uniform in [0, 0.05 L], {n_cand} candidates "
+                     "(LogNormal median 200, clip 20,000); one graph launch per step"),
         "autotune": tuned, "passing_records": n_pass,
         "plain_grim_filter_ms": round(plain_ms, 3),
         "plain_reads_per_s": round(rs.n / (plain_ms / 1e3), 1),
-        "roofline": {"bound": "hbm", "kernel": "k_candidates (plain call)",
-                     "kernel_ms": round(kernel_ms, 3),
-                     "achieved": round(gbytes / (kernel_ms / 1e3), 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(gbytes / (kernel_ms / 1e3) / hbm, 4),
-                     "traffic": traffic_for(args, "candidates", "grim_candidates.cu"),
-                     "algorithmic_bytes": round(gbytes * 1e9)},
+        "kernel_ms_per_launch": {k: round(v, 3) for k, v in prof.items()},
+        "roofline": roof}
+
+
+def ragged_leg(args, g, steps: int = 3, warmup: int = 2) -> dict:
+    """The ragged candidate workload (4M reads) on the headline's genome, for
+    the headline line."""
+    m = ragged_measure(args, g, 0, 4_000_000, steps, warmup)
+    return {"value": round(m["n_reads"] / (m["ms"] / 1e3), 1), "unit": UNIT,
+            "ms_per_step": round(m["ms"], 3), "steps": steps,
+            "pairs_per_s": round(m["n_cand"] / (m["ms"] / 1e3), 1),
+            **{k: v for k, v in m.items() if k not in ("ms", "n_reads", "n_cand")}}
+
+
+def run_ragged(args, rank, world, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1708_04329_gb300 import synth
+
+    n_reads = args.reads if args.reads != DEFAULT_READS else 4_000_000
+    g = synth.human_genome(args.genome)
+    m = ragged_measure(args, g, rank, n_reads, args.steps, args.warmup, dist)
+    ms = max_over_ranks(m["ms"], dist, "cuda")
+    line = {
+        "metric": "reads/s, candidate lists of ragged reads (graph-captured plan)",
+        "value": round(weak_value(m["n_reads"], world, ms), 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": m["workload"], "reads": m["n_reads"], "candidates": m["n_cand"],
+                   "gen_s": m["gen_s"]},
+        "pairs_per_s": round(m["n_cand"] * world / (ms / 1e3), 1),
+        **{k: v for k, v in m.items() if k not in ("ms", "n_reads", "n_cand", "workload", "gen_s")},
     }
-    ceiling = gather_ceiling(nb, vec_bytes, n_cand, st)
-    if ceiling.get("gbs"):
-        ceiling["frac_of_hbm"] = round(ceiling["gbs"] / hbm, 4)
-    line["gather_ceiling"] = ceiling
-    if ceiling.get("rows_per_s"):
-        line["roofline"]["frac_of_gather_ceiling"] = round(
-            n_cand / (kernel_ms / 1e3) / ceiling["rows_per_s"], 4)
-    plan.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -671,12 +875,9 @@ def gather_ceiling(rows: int, row_bytes: int, n: int, st, warmup: int = 3, reps:
 
     if row_bytes not in (128, 512):
         return {"unavailable": f"no probe for {row_bytes}-byte rows"}
-    lib = ctypes.CDLL(str(ROOT / "paper_1708_04329_gb300" / "_lib" / "libgrim_probe.so"))
-    lib.grim_probe_gather.restype = ctypes.c_int
-    lib.grim_probe_gather.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
-                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
-                                      ctypes.c_uint64, ctypes.c_void_p]
-    lib.grim_probe_gather_sink_words.restype = ctypes.c_uint64
+    from bench_helpers import probe
+
+    lib = probe()
     table = torch.randint(-2 ** 31, 2 ** 31 - 1, (rows * row_bytes // 4,), dtype=torch.int32,
                           device="cuda")
     words = int(lib.grim_probe_gather_sink_words())

@@ -99,6 +99,9 @@ typedef struct {
   const uint32_t* coarse_token_major;
   uint64_t num_coarse, num_coarse_pad, coarse_token_major_bytes;
   uint32_t coarse_factor;
+  /* launch shape of the all-bins kernel (grim_build_opts, grim_index_set_shape) */
+  uint32_t cta_threads;      /* threads of its one persistent CTA per SM        */
+  uint32_t read_range_kb;    /* token-row KiB of one read range (the read tile) */
 } grim_index_desc;
 
 /*
@@ -133,7 +136,12 @@ typedef struct {
    * factors shrink the coarse pass but let more super-bins pass it; the best
    * value depends on the genome too (the package's autotuner measures it). */
   uint32_t coarse_factor;
-  uint32_t reserved[7];
+  /* Launch shape of the all-bins kernel (0 = default; see
+   * grim_index_set_shape): CTA threads (512, 640 or 768) and the read tile,
+   * in KiB of token rows per read range (1024 .. 4194304). */
+  uint32_t cta_threads;
+  uint32_t read_range_kb;
+  uint32_t reserved[5];
 } grim_build_opts;
 
 /* The coarse factor grim_build_ex chooses when opts->coarse_factor is 0. */
@@ -149,6 +157,25 @@ int grim_build_host_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q,
 
 /* Fill *out with the index's sizes and device table pointers. */
 int grim_index_info(const grim_index* idx, grim_index_desc* out);
+
+/*
+ * Launch shape of the all-bins kernel for later calls with this index (the
+ * tile sizes the paper ties to its parallel width p, §Parameter Evaluation
+ * Results: how many bins' bits one fetch covers and how many reads reuse
+ * it).  The bin tile is fixed by shared memory (1024 bins up to q = 5, 256
+ * at q = 6; the coarse factor of grim_build_opts sets how many bins a
+ * super-bin holds); this sets the rest:
+ *   cta_threads    threads of the one persistent CTA per SM: 512, 640 or 768
+ *                  (more warps, fewer registers each); 0 = 640
+ *   read_range_kb  read tile: reads are swept in ranges of about this many
+ *                  KiB of token rows, range by range, so that a range stays
+ *                  in L2 while every CTA sweeps its tiles against it;
+ *                  1024 .. 4194304, 0 = 49152 (48 MiB)
+ * Results do not depend on the shape.  Graph plans take the shape when they
+ * are created.  Not to be called while a filter call with this index runs.
+ * Errors: GRIM_E_ARG (NULL index, a value outside the ranges above).
+ */
+int grim_index_set_shape(grim_index* idx, uint32_t cta_threads, uint32_t read_range_kb);
 
 /*
  * Index persistence (§GRIM-Filter: the bit vectors are generated once per
@@ -263,14 +290,24 @@ int grim_filter_host(const grim_index* idx, const char* reads, const uint64_t* o
  * The caller still passes the inputs and the output arrays (device memory),
  * exactly as for grim_filter.
  *   - Size limit: a call whose scratch (grim_filter_workspace_size(idx,
- *     n_reads, n_cand, cap)) exceeds GRIM_NOALLOC_SCRATCH_BYTES is rejected
- *     with GRIM_E_WORKSPACE before any device work (at q = 5 and 100 bp
- *     reads that is roughly 196 bytes per read plus 18 bytes per unit of cap,
- *     or, for an index with the coarse layout, roughly 1.9 kB per read while
- *     cap stays below 64 records per read).
+ *     n_reads, n_cand, cap), the exact figure to check a batch against)
+ *     exceeds GRIM_NOALLOC_SCRATCH_BYTES (also returned by
+ *     grim_noalloc_scratch_bytes) is rejected with GRIM_E_WORKSPACE before
+ *     any device work.  The per-read part depends on the index, not on the
+ *     reads' own lengths: 2*ts + 4 bytes per read, with ts = the index's
+ *     max_read_len - q + 1 rounded up to a multiple of 16 (196 bytes for an
+ *     index built for 100 bp reads at q = 5, 484 bytes for 250 bp), times 4
+ *     for the token copies of the all-bins mode at q = 6; then 18 bytes per
+ *     record of capacity, which is cap, or max(cap, 64 * n_reads) for an
+ *     index with the coarse layout (room for the coarse pass's survivors),
+ *     whose records take another 4 * coarse_factor bytes each for the
+ *     survivors' expanded candidate lists.
  *   - First call on a device: it looks up the array's device address (once
- *     per device, with that device current); make that first call before
- *     any stream capture.
+ *     per device, with that device current) and keeps it for the life of the
+ *     process; make that first call before any stream capture.  The kept
+ *     address assumes one CUDA context per device for the whole process:
+ *     after cudaDeviceReset the library must be reloaded before this entry
+ *     point is used again.
  *   - Sharing: all calls share the one array and it keeps the last call's
  *     contents (each call clears what must start at zero).  Calls that
  *     overlap on the GPU -- from several host threads, or on several
@@ -278,6 +315,8 @@ int grim_filter_host(const grim_index* idx, const char* reads, const uint64_t* o
  * Errors: as grim_filter.
  */
 #define GRIM_NOALLOC_SCRATCH_BYTES (32u << 20)
+/* GRIM_NOALLOC_SCRATCH_BYTES as compiled into the library. */
+uint64_t grim_noalloc_scratch_bytes(void);
 int grim_filter_noalloc(const grim_index* idx, const char* reads, const uint64_t* offsets,
                         const uint32_t* lens, uint32_t n_reads, const uint16_t* e,
                         const int32_t* cand, const uint64_t* cand_off, uint64_t n_cand,

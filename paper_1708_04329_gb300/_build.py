@@ -3,8 +3,6 @@
 * ``libgrim.so``  -- the CUDA kernels and the C-ABI (``include/grim.h``), built
   by nvcc for sm_103a only.
 * ``libsynth.so`` -- the seeded synthetic-input generator (plain C).
-* ``libgrim_probe.so`` -- a measurement helper for the benchmark: the random
-  gather rate of this GPU, the practical ceiling of the candidate-list path.
 
 Both land in ``paper_1708_04329_gb300/_lib/``.  A build is skipped when the
 library is newer than every source it depends on.
@@ -99,23 +97,11 @@ def build_grim(force: bool = False, extra: list[str] | None = None) -> Path:
     return out
 
 
-def build_probe(force: bool = False) -> Path:
-    LIBDIR.mkdir(exist_ok=True)
-    out = LIBDIR / "libgrim_probe.so"
-    src = CSRC / "probe_gather.cu"
-    if force or _stale(out, [src]):
-        tmp = out.with_suffix(f".so.tmp{os.getpid()}")
-        _run([_nvcc()] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-                                 "--cudart", "static", str(src), "-o", str(tmp)])
-        os.replace(tmp, out)
-    return out
-
-
 def build_all(force: bool = False) -> dict[str, Path]:
     with cf.ThreadPoolExecutor(max_workers=2) as ex:
-        probe = ex.submit(build_probe, force)
-        out = {"synth": build_synth(force), "grim": build_grim(force)}
-        out["probe"] = probe.result()
+        synth = ex.submit(build_synth, force)
+        out = {"grim": build_grim(force)}
+        out["synth"] = synth.result()
     return out
 
 

@@ -1,13 +1,23 @@
 """Autotuner for the filter's tile shapes, by measurement on the GPU.
 
-Two shapes are tuned, each by timing real filter runs on a sample of the
-caller's reads with CUDA events:
+The shapes are tuned by timing real filter runs on a sample of the caller's
+reads with CUDA events:
 
-* the bin tile of the all-bins mode: the coarse factor f (bins per super-bin
-  of the coarse table).  Candidates are the power-of-two neighbours of the
-  presence-model default; each needs its own index build (~0.1 s at 3.1 Gbp).
-* the read tile of the candidate mode: how many candidate gathers each lane
-  group keeps in flight (1, 2, 4 or 8), timed through graph-captured plans.
+* all-bins mode (``tune_all_bins``), by coordinate descent:
+  - the bin tile: the coarse factor f (bins per super-bin of the coarse
+    table) among the power-of-two neighbours of the presence-model default,
+    or one exact pass over every bin (f = 0); each needs its own index build
+    (~0.1 s at 3.1 Gbp);
+  - the CTA size of the persistent kernel (512, 640 or 768 threads: warps
+    per SM against registers per thread);
+  - the read tile: KiB of token rows per read range (a range stays in L2
+    while every CTA sweeps its tiles against it).
+  The paper ties its throughput to the same two widths: how many bins one
+  row fetch covers and how many reads share it (§Parameter Evaluation
+  Results, parallel width p).
+* candidate mode (``tune_candidate_unroll``): how many candidate gathers
+  each lane group keeps in flight (1, 2, 4 or 8), timed through
+  graph-captured plans.
 
 Results are cached in a JSON file keyed by the problem's shape and the GPU,
 so a service tunes once per (reference, parameters, device).
@@ -66,32 +76,80 @@ def _time(fn, repeats: int) -> float:
     return statistics.median(times)
 
 
-def tune_coarse_factor(ref, B: int, q: int, max_read_len: int, sample: dict,
-                       factors: list[int] | None = None, repeats: int = 2,
-                       cache: Path | None = DEFAULT_CACHE) -> dict:
-    """Pick the coarse factor for all-bins filtering of reads like `sample`.
+def _token_bytes(n_reads: int, q: int, max_read_len: int) -> int:
+    """Token-row bytes the all-bins kernel sweeps for n_reads reads: a 16-token
+    aligned row of uint16 per read, in four copies at q = 6."""
+    ts = (max_read_len - q + 1 + 15) // 16 * 16
+    return n_reads * ts * 2 * (4 if q >= 6 else 1)
+
+
+def tune_all_bins(ref, B: int, q: int, max_read_len: int, sample: dict,
+                  factors: list[int] | None = None, threads=(512, 640, 768),
+                  ranges_kb=(12 << 10, 24 << 10, 48 << 10, 96 << 10), repeats: int = 2,
+                  cache: Path | None = DEFAULT_CACHE) -> dict:
+    """Pick the all-bins mode's tile shapes for reads like `sample`.
 
     ref: uint8 CUDA tensor of the reference; sample: the grim_filter keyword
-    arguments (reads, offsets, lens, e) of a few thousand to a few hundred
-    thousand representative reads.  Returns {"factor": f, "ms": {f: ms}}.
+    arguments (reads, offsets, lens, e) of representative reads, enough to
+    fill the GPU (a few hundred thousand).  Read ranges are only compared
+    when the sample's token rows span more than one of them.  Returns
+    {"factor": f (0 = one exact pass), "cta_threads": t, "read_range_kb": r,
+    "ms": {trial: ms}}; build the index with grim_build_ex(..., coarse_factor=f,
+    cta_threads=t, read_range_kb=r) and, for f = 0, without the coarse layout.
     """
-    key = f"coarse|{int(ref.numel())}|{B}|{q}|{max_read_len}|{int(sample['lens'].numel())}|{_device_name()}"
+    n = int(sample["lens"].numel())
+    key = (f"allbins|{int(ref.numel())}|{B}|{q}|{max_read_len}|{n}|"
+           f"{tuple(threads)}|{tuple(ranges_kb)}|{_device_name()}")
     table = _load(cache)
     if key in table:
         return table[key]
     if factors is None:
         f0 = grim.grim_default_coarse_factor(B, q, max_read_len)
-        factors = sorted({max(2, f0 // 2), f0, min(64, f0 * 2)})
+        factors = [0] + sorted({max(2, f0 // 2), f0, min(64, f0 * 2)})
     ws = grim.Workspace()
     ms = {}
+
+    def build(f):
+        layouts = grim.GRIM_LAYOUT_TOKEN_MAJOR if f == 0 else grim.GRIM_LAYOUT_ALL
+        return grim.grim_build_ex(ref, B, q, max_read_len, layouts, f)
+
+    def run(index):
+        return _time(lambda: grim.grim_filter(index, **sample, workspace=ws), repeats)
+
+    # 1. bin tile, at the default launch shape
     for f in factors:
-        idx = grim.grim_build_ex(ref, B, q, max_read_len, grim.GRIM_LAYOUT_ALL, f)
+        index = build(f)
         try:
-            ms[f] = _time(lambda: grim.grim_filter(idx, **sample, workspace=ws), repeats)
+            ms[f"f={f}"] = run(index)
         finally:
-            idx.close()
-    best = min(ms, key=ms.get)
-    out = {"factor": int(best), "ms": {str(k): round(v, 3) for k, v in ms.items()}}
+            index.close()
+    best_f = min(factors, key=lambda f: ms[f"f={f}"])
+    index = build(best_f)
+    try:
+        d = index.desc
+        best_t, best_r = d.cta_threads, d.read_range_kb
+        base = ms[f"f={best_f}"]
+        # 2. CTA size
+        for t in threads:
+            if t == best_t:
+                continue
+            grim.grim_index_set_shape(index, t, best_r)
+            ms[f"threads={t}"] = run(index)
+        ms[f"threads={best_t}"] = base
+        best_t = min(threads, key=lambda t: ms[f"threads={t}"])
+        base = ms[f"threads={best_t}"]
+        # 3. read tile: only sizes that split the sample into several ranges
+        tb = _token_bytes(n, q, max_read_len)
+        tried = [r for r in ranges_kb if (r << 10) < tb and r != best_r]
+        for r in tried:
+            grim.grim_index_set_shape(index, best_t, r)
+            ms[f"range_kb={r}"] = run(index)
+        ms[f"range_kb={best_r}"] = base
+        best_r = min([best_r] + tried, key=lambda r: ms[f"range_kb={r}"])
+    finally:
+        index.close()
+    out = {"factor": int(best_f), "cta_threads": int(best_t), "read_range_kb": int(best_r),
+           "ms": {k: round(v, 3) for k, v in ms.items()}, "sample_reads": n}
     table[key] = out
     _store(cache, table)
     return out

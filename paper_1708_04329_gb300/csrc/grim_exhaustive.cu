@@ -4,7 +4,7 @@
 //
 // GB300 mapping
 // -------------
-// * A persistent CTA (one per SM, up to 640 threads) takes work items (tile
+// * A persistent CTA (one per SM, 512 to 768 threads) takes work items (tile
 //   of TW*32 bins, range of reads).  The tile -- 4^q rows x TW words of the
 //   token-major table -- is staged in shared memory once per item and reused
 //   by every read of the range.  TW = 32 (1024 bins, 128 KB at q = 5) up to q = 5 and
@@ -50,14 +50,17 @@
 namespace grim {
 namespace {
 
-// 20 warps, 96 registers a thread: no spills.  On GB300 this beat 24 warps
-// at 80 registers (which spill a few words) by 4.7% at q = 5 and 2.4% at
-// q = 6; 16, 18 and 28 warps were also slower than 20.
-constexpr int kMaxThreads = 640;
+// CTA sizes built (the register cap follows from one CTA per SM): 512
+// threads (128 registers), 640 (96) and 768 (80).  640 is the default: on
+// GB300 it beat 768 threads (which spill a few words) by 4.7% at q = 5 and
+// 2.4% at q = 6, and 512 by 2.6%; the autotuner can pick another.
+constexpr uint32_t kDefaultThreads = 640;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
-constexpr uint64_t kRangeTokenBytes = 48ull << 20;  // token rows of one read range: L2-resident
-constexpr uint32_t kSlotBlocksNarrow = 1;           // slot blocks per read, 256-bin tiles
+// token rows of one read range: small enough to stay in L2 while every CTA
+// sweeps its tiles against the range
+constexpr uint64_t kDefaultRangeBytes = 48ull << 20;
+constexpr uint32_t kSlotBlocksNarrow = 1;  // slot blocks per read, 256-bin tiles
 
 #define LOP3(d, a, b, c, lut) \
   asm("lop3.b32 %0, %1, %2, %3, " #lut ";" : "=r"(d) : "r"(a), "r"(b), "r"(c))
@@ -134,6 +137,7 @@ struct ExhArgs {
   uint32_t slot_bytes;  // bytes of a group slot: two token rows
   uint32_t slot_blocks; // 16-token blocks a slot row holds; later blocks come from L2
   uint32_t c_row, c_hi, c_lo;  // TW*4, 65536, -65536: multipliers of the address math
+  uint64_t range_bytes;        // token-row bytes of one read range (the read tile)
   Ctl* ctl;
 };
 
@@ -186,8 +190,8 @@ __device__ __forceinline__ void add_block(Counters<P>& c, const uint32_t (&tw)[8
   }
 }
 
-template <int P, int TW>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
+template <int P, int TW, int NT>
+__global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
   constexpr uint32_t kRowBytes = TW * 4;     // one token's row of a tile
   constexpr uint32_t GL = TW / 4;            // lanes per group (one read)
   constexpr uint32_t kGroupMask = (1u << GL) - 1u;
@@ -211,7 +215,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
   // every read's tokens from DRAM
   uint32_t n_ranges = (4u * a.sms + a.n_tiles - 1) / a.n_tiles;
   const uint64_t token_bytes = (uint64_t)n_reads * a.rv.ts * 2u * a.rv.copies;
-  const uint32_t l2_ranges = (uint32_t)((token_bytes + kRangeTokenBytes - 1) / kRangeTokenBytes);
+  const uint32_t l2_ranges = (uint32_t)((token_bytes + a.range_bytes - 1) / a.range_bytes);
   n_ranges = max(n_ranges, l2_ranges);
   n_ranges = min(n_ranges, (n_reads + 63) / 64);
   n_ranges = max(n_ranges, 1u);
@@ -426,24 +430,36 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_exhaustive(ExhArgs a) {
   }
 }
 
-template <int P, int TW>
+template <int P, int TW, int NT>
 void launch_p(const ExhArgs& a, size_t smem, uint32_t threads, uint32_t grid, cudaStream_t st,
               const char* name) {
-  cudaFuncSetAttribute(k_exhaustive<P, TW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_exhaustive<P, TW, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
   ProfScope ps(name, st);
-  k_exhaustive<P, TW><<<grid, threads, smem, st>>>(a);
+  k_exhaustive<P, TW, NT><<<grid, threads, smem, st>>>(a);
+}
+
+template <int TW, int NT>
+void launch_nt(const ExhArgs& a, size_t smem, uint32_t threads, uint32_t grid, uint32_t max_d,
+               cudaStream_t st, const char* name) {
+  // the counters need 2^P > D' (D' <= 255)
+  if (max_d < 32) launch_p<5, TW, NT>(a, smem, threads, grid, st, name);
+  else if (max_d < 64) launch_p<6, TW, NT>(a, smem, threads, grid, st, name);
+  else if (max_d < 128) launch_p<7, TW, NT>(a, smem, threads, grid, st, name);
+  else launch_p<8, TW, NT>(a, smem, threads, grid, st, name);
 }
 
 template <int TW>
-void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, cudaStream_t st,
-               const char* name) {
+void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, uint32_t nt,
+               cudaStream_t st, const char* name) {
   constexpr uint32_t kRowBytes = TW * 4, GL = TW / 4, kTileBinsT = TW * 32;
   a.n_tiles = (uint32_t)(ix.num_bins_pad / kTileBinsT);
   a.sms = sms;
   a.c_row = kRowBytes;
-  // the largest CTA whose tile and group slots fit in shared memory
+  // the largest CTA up to the built size whose tile and group slots fit in
+  // shared memory
   const size_t tile_bytes = (size_t)(ix.r4 + 2) * kRowBytes;
-  uint32_t threads = kMaxThreads;
+  uint32_t threads = nt;
   while (threads > 64 && tile_bytes + (size_t)(threads / GL) * a.slot_bytes + 32 > kSmemLimit)
     threads -= 32;
   const size_t smem = tile_bytes + (size_t)(threads / GL) * a.slot_bytes + 32;
@@ -455,20 +471,24 @@ void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, cu
     const uint64_t items = (uint64_t)a.n_tiles * ((a.rv.n_reads + per_item - 1) / per_item);
     if (items < grid) grid = (uint32_t)(items ? items : 1);
   }
-  // the counters need 2^P > D' (D' <= 255)
-  if (max_d < 32) launch_p<5, TW>(a, smem, threads, grid, st, name);
-  else if (max_d < 64) launch_p<6, TW>(a, smem, threads, grid, st, name);
-  else if (max_d < 128) launch_p<7, TW>(a, smem, threads, grid, st, name);
-  else launch_p<8, TW>(a, smem, threads, grid, st, name);
+  if (nt == 512) launch_nt<TW, 512>(a, smem, threads, grid, max_d, st, name);
+  else if (nt == 768) launch_nt<TW, 768>(a, smem, threads, grid, max_d, st, name);
+  else launch_nt<TW, 640>(a, smem, threads, grid, max_d, st, name);
 }
 
 }  // namespace
 
 uint32_t exhaustive_tile_bins(uint32_t r4) { return r4 <= 1024 ? 32u * 32u : 8u * 32u; }
 
+bool exhaustive_shape_ok(uint32_t threads, uint32_t range_kb) {
+  const bool t_ok = threads == 0 || threads == 512 || threads == 640 || threads == 768;
+  const bool r_ok = range_kb == 0 || (range_kb >= 1024 && range_kb <= (4u << 20));
+  return t_ok && r_ok;
+}
+
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st, const char* prof_name,
-                       Live live) {
+                       Live live, ExhShape shape) {
   if (rv.n_reads == 0) return;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -494,9 +514,11 @@ void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec
   a.slot_bytes = (2u * a.row_stride + 127u) / 128u * 128u + 32u;
   a.c_hi = 65536u;
   a.c_lo = 0u - 65536u;
+  a.range_bytes = shape.range_kb ? (uint64_t)shape.range_kb << 10 : kDefaultRangeBytes;
   a.ctl = ctl;
-  if (ix.r4 <= 1024) launch_tw<32>(a, ix, max_d, (uint32_t)sms, st, prof_name);
-  else launch_tw<8>(a, ix, max_d, (uint32_t)sms, st, prof_name);
+  const uint32_t nt = shape.threads ? shape.threads : kDefaultThreads;
+  if (ix.r4 <= 1024) launch_tw<32>(a, ix, max_d, (uint32_t)sms, nt, st, prof_name);
+  else launch_tw<8>(a, ix, max_d, (uint32_t)sms, nt, st, prof_name);
 }
 
 }  // namespace grim

@@ -135,10 +135,20 @@ void launch_check_candidates(const uint64_t* cand_off, uint32_t n_reads, uint64_
 
 // bins per tile of the all-bins kernel for a table of r4 = 4^q rows
 uint32_t exhaustive_tile_bins(uint32_t r4);
+// Launch shape of the all-bins kernel (0 = the default): CTA threads (512,
+// 640 or 768; one persistent CTA per SM) and the token-row bytes of one read
+// range in KiB (reads are swept range by range so a range's token rows stay
+// in L2 while the CTAs sweep their tiles).
+struct ExhShape {
+  uint32_t threads;
+  uint32_t range_kb;
+};
+bool exhaustive_shape_ok(uint32_t threads, uint32_t range_kb);
 // max_d: the batch's largest miss budget (sizes the bit-sliced counters)
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st,
-                       const char* prof_name = "exhaustive", Live live = {false, 0});
+                       const char* prof_name = "exhaustive", Live live = {false, 0},
+                       ExhShape shape = {0, 0});
 // unroll: candidate gathers in flight per lane group (1, 2, 4 or 8; 0 =
 // default).  check_ids: the lists are the caller's; an id outside
 // [0, num_bins) sets kStatusBadCand (and is not gathered).  Internal lists
@@ -260,6 +270,7 @@ struct grim_index {
   grim::IndexView cv;  // super-bins of `factor` bins: coarse token-major table
   uint32_t factor;
   uint32_t layouts;
+  grim::ExhShape shape;  // launch shape of the all-bins kernel (grim_index_set_shape)
   uint32_t* tm;
   uint32_t* bm;
   uint32_t* ctm;

@@ -23,8 +23,10 @@ std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device.  In host code the array's name is only a host-side handle, so
-// the kernels must be given this address instead.
+// per device and kept for the life of the process (one CUDA context per
+// device is assumed: a cudaDeviceReset would leave the kept address stale).
+// In host code the array's name is only a host-side handle, so the kernels
+// must be given this address instead.
 int scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -63,3 +65,5 @@ extern "C" int grim_filter_noalloc(const grim_index* idx, const char* reads,
   return grim_filter(idx, reads, offsets, lens, n_reads, e, cand, cand_off, n_cand, out_read,
                      out_bin, out_count, cap, n_out, scratch, GRIM_NOALLOC_SCRATCH_BYTES, stream);
 }
+
+extern "C" uint64_t grim_noalloc_scratch_bytes(void) { return GRIM_NOALLOC_SCRATCH_BYTES; }

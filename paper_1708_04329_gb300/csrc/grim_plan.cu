@@ -169,7 +169,8 @@ int capture(grim_plan* p) {
         idx->cv.num_bins > 1 ? bit_length(idx->cv.num_bins - 1) : 0;
     if (p->f) {
       const Live coarse{true, kPathCoarse};
-      launch_exhaustive(idx->cv, rv, ra, cbits, max_d, p->ctl, st, "exhaustive_coarse", coarse);
+      launch_exhaustive(idx->cv, rv, ra, cbits, max_d, p->ctl, st, "exhaustive_coarse", coarse,
+                        idx->shape);
       k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlAfterCoarse, 1, has_exact, rcap);
       const RecordsView surv = sort_records(ra, rb, rcap, read_bits + cbits, ws + L.hist, st,
                                             &p->ctl->n_surv, p->ctl, kPathCoarse);
@@ -180,7 +181,7 @@ int capture(grim_plan* p) {
     }
     if (has_exact) {
       const Live exact{true, kPathExact};
-      launch_exhaustive(v, rv, ra, bin_bits, max_d, p->ctl, st, "exhaustive", exact);
+      launch_exhaustive(v, rv, ra, bin_bits, max_d, p->ctl, st, "exhaustive", exact, idx->shape);
     }
     k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlFinal, 0, 0, 0);
     if (p->f) {

@@ -53,6 +53,7 @@ EXPORTS = (
     "grim_server_create", "grim_server_submit", "grim_server_wait", "grim_server_take",
     "grim_server_stats_get", "grim_server_free", "grim_save", "grim_load",
     "grim_reverse_complement", "grim_server_cancel", "grim_trim_scratch", "grim_set_allocator",
+    "grim_noalloc_scratch_bytes", "grim_index_set_shape",
 )
 
 
@@ -73,7 +74,8 @@ class _Desc(C.Structure):
                 ("bin_major", C.c_void_p), ("token_major_bytes", C.c_uint64),
                 ("bin_major_bytes", C.c_uint64), ("coarse_token_major", C.c_void_p),
                 ("num_coarse", C.c_uint64), ("num_coarse_pad", C.c_uint64),
-                ("coarse_token_major_bytes", C.c_uint64), ("coarse_factor", C.c_uint32)]
+                ("coarse_token_major_bytes", C.c_uint64), ("coarse_factor", C.c_uint32),
+                ("cta_threads", C.c_uint32), ("read_range_kb", C.c_uint32)]
 
 
 class _Stats(C.Structure):
@@ -83,7 +85,8 @@ class _Stats(C.Structure):
 
 
 class _BuildOpts(C.Structure):
-    _fields_ = [("coarse_factor", C.c_uint32), ("reserved", C.c_uint32 * 7)]
+    _fields_ = [("coarse_factor", C.c_uint32), ("cta_threads", C.c_uint32),
+                ("read_range_kb", C.c_uint32), ("reserved", C.c_uint32 * 5)]
 
 
 class _PlanDesc(C.Structure):
@@ -151,6 +154,8 @@ def _lib() -> C.CDLL:
         lib.grim_default_coarse_factor.argtypes = [u32, u32, u32]
         lib.grim_index_info.restype = i32
         lib.grim_index_info.argtypes = [vp, C.POINTER(_Desc)]
+        lib.grim_index_set_shape.restype = i32
+        lib.grim_index_set_shape.argtypes = [vp, u32, u32]
         lib.grim_free.restype = None
         lib.grim_free.argtypes = [vp]
         lib.grim_strerror.restype = C.c_char_p
@@ -166,6 +171,8 @@ def _lib() -> C.CDLL:
         lib.grim_filter_host.argtypes = fargs + [vp]
         lib.grim_filter_noalloc.restype = i32
         lib.grim_filter_noalloc.argtypes = fargs + [vp]
+        lib.grim_noalloc_scratch_bytes.restype = u64
+        lib.grim_noalloc_scratch_bytes.argtypes = []
         lib.grim_loc_to_bin.restype = u64
         lib.grim_loc_to_bin.argtypes = [vp, u64]
         lib.grim_edits_for_rate.restype = u32
@@ -245,6 +252,28 @@ def _dptr(t, what: str, esize: int | None = None) -> int:
     return t.data_ptr()
 
 
+def _check_out(out, what: str) -> int:
+    """Validate a caller's (read, bin, count) output triple of CUDA tensors and
+    return its capacity.  The kernels write up to `cap` records into each of
+    the three arrays, so all three must hold `cap` elements of the right
+    width on the current device."""
+    torch = _torch()
+    if len(out) != 3:
+        raise ValueError(f"{what}: out must be a (read, bin, count) triple")
+    cap = int(out[0].numel())
+    dev = torch.cuda.current_device()
+    for t, name, es in zip(out, ("out_read", "out_bin", "out_count"), (4, 4, 1)):
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{what}: {name} must be a CUDA tensor on the current device")
+        if t.element_size() != es or t.is_floating_point():
+            raise ValueError(f"{what}: {name} must have {es}-byte integer elements")
+        if not t.is_contiguous():
+            raise ValueError(f"{what}: {name} must be contiguous")
+        if int(t.numel()) != cap:
+            raise ValueError(f"{what}: the three output arrays must have the same length")
+    return cap
+
+
 def _hptr(a, what: str, dtype) -> tuple[int, object]:
     """Host pointer of an array converted to dtype (keeps the buffer alive)."""
     if a is None:
@@ -300,6 +329,8 @@ class IndexDesc:
     num_coarse_pad: int = 0
     coarse_token_major_bytes: int = 0
     coarse_factor: int = 0
+    cta_threads: int = 0
+    read_range_kb: int = 0
 
 
 class GrimIndex:
@@ -386,10 +417,12 @@ def grim_build_host(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_
 
 
 def grim_build_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
-                  coarse_factor: int = 0, stream=None) -> GrimIndex:
+                  coarse_factor: int = 0, stream=None, cta_threads: int = 0,
+                  read_range_kb: int = 0) -> GrimIndex:
     """grim_build_ex: grim_build with build options (``coarse_factor``: bins per
-    super-bin of the coarse table, 0 = the library default)."""
-    opts = _BuildOpts(coarse_factor)
+    super-bin of the coarse table; ``cta_threads``, ``read_range_kb``: the
+    all-bins kernel's launch shape; 0 = the library default)."""
+    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb)
     h = C.c_void_p()
     rc = _lib().grim_build_ex(_dptr(ref, "ref", 1), ref.numel(), B, q, max_read_len, layouts,
                               C.byref(opts), _stream_ptr(stream), C.byref(h))
@@ -399,11 +432,12 @@ def grim_build_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LA
 
 
 def grim_build_host_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
-                       coarse_factor: int = 0, stream=None) -> GrimIndex:
+                       coarse_factor: int = 0, stream=None, cta_threads: int = 0,
+                       read_range_kb: int = 0) -> GrimIndex:
     """grim_build_host_ex: grim_build_host with build options."""
     p, keep = _hptr(ref, "ref", np.uint8)
     n = keep.numel() if hasattr(keep, "numel") else keep.size
-    opts = _BuildOpts(coarse_factor)
+    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb)
     h = C.c_void_p()
     rc = _lib().grim_build_host_ex(p, n, B, q, max_read_len, layouts, C.byref(opts),
                                    _stream_ptr(stream), C.byref(h))
@@ -486,7 +520,17 @@ def grim_index_info(index: GrimIndex) -> IndexDesc:
     return IndexDesc(d.ref_len, d.num_bins, d.num_bins_pad, d.B, d.q, d.ext, d.max_read_len,
                      d.layouts, d.words_per_bin, d.token_major or 0, d.bin_major or 0,
                      d.token_major_bytes, d.bin_major_bytes, d.coarse_token_major or 0,
-                     d.num_coarse, d.num_coarse_pad, d.coarse_token_major_bytes, d.coarse_factor)
+                     d.num_coarse, d.num_coarse_pad, d.coarse_token_major_bytes, d.coarse_factor,
+                     d.cta_threads, d.read_range_kb)
+
+
+def grim_index_set_shape(index: GrimIndex, cta_threads: int = 0, read_range_kb: int = 0) -> None:
+    """Launch shape of the all-bins kernel for later calls with this index:
+    CTA threads (512, 640 or 768) and the read tile in KiB of token rows per
+    read range; 0 restores a default."""
+    rc = _lib().grim_index_set_shape(index.handle, cta_threads, read_range_kb)
+    if rc != GRIM_OK:
+        raise GrimError(rc, "grim_index_set_shape")
 
 
 def grim_free(index: GrimIndex) -> None:
@@ -574,7 +618,7 @@ def grim_filter(index: GrimIndex, reads, offsets, lens, e, cand=None, cand_off=N
     n_cand = int(cand.numel()) if cand is not None else 0
     user_out = out is not None
     if out is not None:
-        cap = int(out[0].numel())
+        cap = _check_out(out, "grim_filter")
     elif cap is None:
         cap = 4 * n_reads + 1024
     if out is None:
@@ -681,8 +725,10 @@ def grim_filter_host(index: GrimIndex, reads, offsets, lens, e, cand=None, cand_
     return o_r[:n], o_b[:n], o_c[:n]
 
 
-#: bytes of the fixed device scratch array grim_filter_noalloc uses
-GRIM_NOALLOC_SCRATCH_BYTES = 32 << 20
+def grim_noalloc_scratch_bytes() -> int:
+    """Bytes of the fixed device scratch array grim_filter_noalloc uses (the
+    library's own figure, so callers size batches against the real limit)."""
+    return int(_lib().grim_noalloc_scratch_bytes())
 
 
 def grim_filter_noalloc(index: GrimIndex, reads, offsets, lens, e, out, cand=None, cand_off=None,
@@ -691,14 +737,14 @@ def grim_filter_noalloc(index: GrimIndex, reads, offsets, lens, e, out, cand=Non
     allocation, for callers that cannot allocate (a process whose memory
     manager owns the whole GPU, or a serving loop that keeps cudaMalloc off
     its request path).  Scratch comes from one fixed array inside the library
-    (``GRIM_NOALLOC_SCRATCH_BYTES``), shared by all calls: calls must not
+    (``grim_noalloc_scratch_bytes()`` bytes), shared by all calls: calls must not
     overlap on the GPU.  ``out`` is the caller's (read, bin, count) triple of
     CUDA tensors; returns views of its first n_out records.  Raises
     GrimError(GRIM_E_WORKSPACE) when the call needs more scratch than the
-    array holds."""
+    array holds (``grim_noalloc_scratch_bytes()``)."""
     n_reads = int(lens.numel())
     n_cand = int(cand.numel()) if cand is not None else 0
-    cap = int(out[0].numel())
+    cap = _check_out(out, "grim_filter_noalloc")
     n_out = C.c_uint64(0)
     rc = _lib().grim_filter_noalloc(
         index.handle, _dptr(reads, "reads", 1) if reads.numel() else 0, _dptr(offsets, "offsets", 8),

@@ -35,6 +35,11 @@ def test_library_exports_every_declared_symbol():
 def test_host_helpers_without_gpu():
     from paper_1708_04329_gb300 import grim
 
+    # the no-allocation entry point's scratch size, as the header states it
+    hdr = (ROOT / "include" / "grim.h").read_text()
+    m = re.search(r"#define GRIM_NOALLOC_SCRATCH_BYTES \((\d+)u << (\d+)\)", hdr)
+    assert m and grim.grim_noalloc_scratch_bytes() == int(m.group(1)) << int(m.group(2))
+
     assert grim.grim_strerror(grim.GRIM_E_OVERFLOW).startswith("more passing records")
     assert grim.grim_strerror(0) == "ok"
     # Fig. 4 caption: e = ceil(L * error rate)
@@ -81,12 +86,33 @@ def C_void():
 
 
 def test_gather_probe_library_exports():
-    """The benchmark's random-gather probe (a measurement helper beside the
-    filter) builds and exports its two entry points."""
-    from paper_1708_04329_gb300 import _build
+    """The benchmark's random-gather probe (a measurement helper in
+    bench_helpers/, apart from the filter library) builds and exports its two
+    entry points."""
+    import bench_helpers
 
-    path = _build.build_probe()
+    path = bench_helpers.build_probe()
     out = subprocess.run(["nm", "-D", "--defined-only", str(path)], capture_output=True, text=True,
                          check=True).stdout
     exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
     assert {"grim_probe_gather", "grim_probe_gather_sink_words"} <= exported
+
+
+def test_launch_shape_options_checked_before_any_device_work():
+    """grim_build_ex refuses an all-bins launch shape it does not build (CTA
+    sizes other than 512/640/768, read ranges outside 1 MiB..4 GiB) before it
+    touches the reference pointer, and grim_index_set_shape refuses a NULL
+    index."""
+    import ctypes
+
+    from paper_1708_04329_gb300 import grim
+
+    lib = grim._lib()
+    h = ctypes.c_void_p()
+    fake_ref = ctypes.c_void_p(16)  # never dereferenced: the options fail first
+    for threads, range_kb in ((600, 0), (1024, 0), (0, 512), (0, (4 << 20) + 1)):
+        opts = grim._BuildOpts(0, threads, range_kb)
+        rc = lib.grim_build_ex(fake_ref, 1000, 200, 5, 100, 7, ctypes.byref(opts), None,
+                               ctypes.byref(h))
+        assert rc == grim.GRIM_E_ARG, (threads, range_kb)
+    assert lib.grim_index_set_shape(None, 640, 0) == grim.GRIM_E_ARG

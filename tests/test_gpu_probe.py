@@ -1,5 +1,5 @@
-"""The benchmark's random-gather probe (a measurement helper built beside the
-filter library) runs for both vector sizes and every unroll, and rejects bad
+"""The benchmark's random-gather probe (a measurement helper in bench_helpers/,
+apart from the filter library) runs for both vector sizes and every unroll, and rejects bad
 arguments on the host before any launch."""
 import ctypes
 
@@ -11,15 +11,9 @@ pytestmark = pytest.mark.gpu
 
 
 def _lib():
-    from paper_1708_04329_gb300 import _build
+    from bench_helpers import probe
 
-    lib = ctypes.CDLL(str(_build.build_probe()))
-    lib.grim_probe_gather.restype = ctypes.c_int
-    lib.grim_probe_gather.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
-                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
-                                      ctypes.c_uint64, ctypes.c_void_p]
-    lib.grim_probe_gather_sink_words.restype = ctypes.c_uint64
-    return lib
+    return probe()
 
 
 def test_gather_probe_runs_and_checks_arguments():

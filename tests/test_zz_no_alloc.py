@@ -77,8 +77,9 @@ def test_noalloc_refuses_calls_beyond_its_scratch(setup):
 
     idx, first, _ = setup
     kw = dev_reads(first)
-    too_big = grim.GRIM_NOALLOC_SCRATCH_BYTES // 18 + 1  # output capacity alone overflows it
-    assert grim.grim_filter_workspace_size(idx, first.n, 0, too_big) > grim.GRIM_NOALLOC_SCRATCH_BYTES
+    limit = grim.grim_noalloc_scratch_bytes()
+    too_big = limit // 18 + 1  # output capacity alone overflows it
+    assert grim.grim_filter_workspace_size(idx, first.n, 0, too_big) > limit
     with pytest.raises(grim.GrimError) as ei:
         grim.grim_filter_noalloc(idx, **kw, out=_outs(too_big))
     assert ei.value.code == grim.GRIM_E_WORKSPACE
