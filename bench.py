@@ -79,6 +79,9 @@ def parse_args():
                    help="ragged workload: candidate gathers in flight (0 = autotune)")
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="serve workload: length of the measured arrival trace")
+    p.add_argument("--serve-chunk", type=int, default=0,
+                   help="serve workload: cut requests into chunks of at most this many reads "
+                        "(0: whole requests)")
     p.add_argument("--workload", default="human", choices=["human", "finer", "ragged", "serve"],
                    help="human: B=200, q=5, L=100, e=5 (the headline); finer: B=100, q=6, "
                         "L=150, e=7 on the same genome; ragged: candidate lists for reads of "
@@ -88,7 +91,7 @@ def parse_args():
                         "the library's with --no-tune)")
     p.add_argument("--no-tune", action="store_true",
                    help="skip the all-bins autotuner (library default tile shapes)")
-    p.add_argument("--tune-reads", type=int, default=200_000,
+    p.add_argument("--tune-reads", type=int, default=100_000,
                    help="reads of the batch the all-bins autotuner times its trials on")
     p.add_argument("--no-legs", action="store_true",
                    help="headline only: skip the one-pass exact, ragged and finer-index legs")
@@ -301,10 +304,11 @@ def all_bins_shape(args, w, dev, ref) -> dict:
 
     if args.coarse_factor or args.no_tune:
         return {"tuned": False, "factor": args.coarse_factor, "cta_threads": 0,
-                "read_range_kb": 0, "layouts": grim.GRIM_LAYOUT_ALL}
+                "read_range_kb": 0, "read_switch": 0, "layouts": grim.GRIM_LAYOUT_ALL}
     t0 = time.perf_counter()
     out = autotune.tune_all_bins(ref, w["B"], w["q"], w["max_read_len"],
-                                 sample_of(dev, w["reads"], args.tune_reads), cache=None)
+                                 sample_of(dev, w["reads"], args.tune_reads), repeats=1,
+                                 cache=None)
     out = dict(out, tuned=True, tune_s=round(time.perf_counter() - t0, 1))
     out["layouts"] = grim.GRIM_LAYOUT_ALL if out["factor"] else grim.GRIM_LAYOUT_BOTH
     return out
@@ -353,7 +357,8 @@ def run_native(args, rank, world, local):
         evs[0].record(st)
         idx = grim.grim_build_ex(ref, B, q, mrl, shape["layouts"], shape["factor"], stream=st,
                                  cta_threads=shape["cta_threads"],
-                                 read_range_kb=shape["read_range_kb"])
+                                 read_range_kb=shape["read_range_kb"],
+                                 read_switch=shape["read_switch"])
         evs[1].record(st)
         a = grim.grim_filter(idx, **dev, out=outs[0], workspace=ws, stream=st)
         evs[2].record(st)
@@ -516,7 +521,8 @@ def exact_leg(w, dev, ref, shape, st, n_sm, sm_max, args, steps: int = 2, warmup
     rs = w["reads"]
     idx = grim.grim_build_ex(ref, w["B"], w["q"], w["max_read_len"], grim.GRIM_LAYOUT_TOKEN_MAJOR,
                              stream=st, cta_threads=shape["cta_threads"],
-                             read_range_kb=shape["read_range_kb"])
+                             read_range_kb=shape["read_range_kb"],
+                             read_switch=shape["read_switch"])
     cap = 8 * rs.n + 4096
     ws = grim.Workspace()
     res = {}
@@ -635,7 +641,8 @@ def run_e2e(args, w, st, shape):
         idx = grim.grim_build_host_ex(h["ref"], w["B"], w["q"], w["max_read_len"],
                                       shape["layouts"], shape["factor"], stream=st,
                                       cta_threads=shape["cta_threads"],
-                                      read_range_kb=shape["read_range_kb"])
+                                      read_range_kb=shape["read_range_kb"],
+                                      read_switch=shape["read_switch"])
         t.append(time.perf_counter())
         a = grim.grim_filter_host(idx, h["seq"], h["off"], h["lens"], h["e"], out=outs[0], stream=st)
         t.append(time.perf_counter())
@@ -1078,7 +1085,7 @@ def run_serve(args, rank, world, local):
     slot_reads = 16384
     srv = grim.grim_server_create(idx, slots=3, max_reads=slot_reads, max_bases=slot_reads * 250,
                                   max_e=int(rs.e.max()), cap=32 * slot_reads,
-                                  mem_budget=8 << 30)
+                                  mem_budget=8 << 30, max_chunk_reads=args.serve_chunk)
     # warm-up, then capacity with the queue kept full (batches/s of the same size mix)
     _serve_trace(srv, rs, synth.request_trace(1.0, 100.0, rs.n, seed=60), paced=False,
                  time_limit_s=2.0)
@@ -1123,6 +1130,7 @@ def run_serve(args, rank, world, local):
                                 "{100,150,250} (.5/.3/.2), e uniform in [0, 0.05 L]; "
                                 f"{args.serve_seconds:.0f} s trace"),
                    "slots": st["slots"], "slot_reads": slot_reads,
+                   "max_chunk_reads": args.serve_chunk,
                    "slot_device_bytes": st["device_bytes"], "gen_s": round(gen_s, 1),
                    "l2": "table (1.98 GB) larger than L2"},
         "offered_batches_per_s": round(best, 1),

@@ -102,6 +102,7 @@ typedef struct {
   /* launch shape of the all-bins kernel (grim_build_opts, grim_index_set_shape) */
   uint32_t cta_threads;      /* threads of its one persistent CTA per SM        */
   uint32_t read_range_kb;    /* token-row KiB of one read range (the read tile) */
+  uint32_t read_switch;      /* GRIM_SWITCH_GROUP, GRIM_SWITCH_WARP, 0 = automatic */
 } grim_index_desc;
 
 /*
@@ -127,6 +128,11 @@ int grim_build(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t m
 int grim_build_host(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len,
                     uint32_t layouts, void* stream, grim_index** out);
 
+/* How the lane groups of a warp in the all-bins kernel take their next read
+ * (grim_index_set_shape). */
+#define GRIM_SWITCH_GROUP 1u /* each group as soon as its read ends             */
+#define GRIM_SWITCH_WARP 2u  /* all groups of a warp together, once all ended   */
+
 /* Build options.  Zero-initialise and set what you need. */
 typedef struct {
   /* bins per super-bin of the coarse table (1..64).  0 chooses the largest
@@ -141,7 +147,8 @@ typedef struct {
    * in KiB of token rows per read range (1024 .. 4194304). */
   uint32_t cta_threads;
   uint32_t read_range_kb;
-  uint32_t reserved[5];
+  uint32_t read_switch;  /* GRIM_SWITCH_* (0 = automatic) */
+  uint32_t reserved[4];
 } grim_build_opts;
 
 /* The coarse factor grim_build_ex chooses when opts->coarse_factor is 0. */
@@ -171,11 +178,22 @@ int grim_index_info(const grim_index* idx, grim_index_desc* out);
  *                  KiB of token rows, range by range, so that a range stays
  *                  in L2 while every CTA sweeps its tiles against it;
  *                  1024 .. 4194304, 0 = 49152 (48 MiB)
+ *   read_switch    GRIM_SWITCH_GROUP, GRIM_SWITCH_WARP, or 0 (automatic):
+ *                  a warp's lane groups each hold one read; taking the next
+ *                  read costs the whole warp the same instructions whether
+ *                  one group or all take one, so WARP lets a group whose read
+ *                  ended early idle until every group's read has ended, and
+ *                  then switches all of them at once (fewer switches, some
+ *                  idle blocks).  Automatic: WARP when every read of the
+ *                  batch spans the same number of 16-token blocks (so no
+ *                  group idles for long), GROUP otherwise; graph plans, whose
+ *                  batches are not known when they are captured, use GROUP
  * Results do not depend on the shape.  Graph plans take the shape when they
  * are created.  Not to be called while a filter call with this index runs.
  * Errors: GRIM_E_ARG (NULL index, a value outside the ranges above).
  */
-int grim_index_set_shape(grim_index* idx, uint32_t cta_threads, uint32_t read_range_kb);
+int grim_index_set_shape(grim_index* idx, uint32_t cta_threads, uint32_t read_range_kb,
+                         uint32_t read_switch);
 
 /*
  * Index persistence (§GRIM-Filter: the bit vectors are generated once per
@@ -417,9 +435,12 @@ void grim_plan_free(grim_plan* plan);
  * device.  The slots' device memory (batch buffers, workspace, pass lists)
  * is bounded by mem_budget.  A request's result is the same as grim_filter
  * of that request alone: the filter works read by read, and each request's
- * records are handed back with its own read numbering.  A merged batch whose
- * pass list exceeds `cap` is split and its requests rerun one per batch; a
- * request alone over `cap` completes with GRIM_E_OVERFLOW.
+ * records are handed back with its own read numbering.  With
+ * max_chunk_reads, large requests are cut into chunks of consecutive reads
+ * that are queued and batched like requests of their own.  A merged batch
+ * whose pass list exceeds `cap` is split and its requests (or chunks) rerun
+ * one per batch; one over `cap` alone completes its request with
+ * GRIM_E_OVERFLOW and the request's total.
  *
  * Requests are validated at submission (read lengths against the index,
  * e <= max_e, sizes against the slot limits, candidate ids and offsets), so
@@ -439,7 +460,13 @@ typedef struct {
   uint64_t max_queued_reads; /* submit returns GRIM_E_BUSY past this many waiting reads
                                 (0: no limit; a request is always taken into an empty queue) */
   uint32_t cand_unroll;      /* as grim_plan_desc                                          */
-  uint32_t reserved[7];
+  /* 0: each request runs whole, in one batch (a request larger than a slot
+   * is refused).  N >= 1 (at most max_reads): a request is cut into chunks
+   * of up to N consecutive reads (and within max_bases and max_cand), which
+   * may run in different slots and batches; the request completes when its
+   * last chunk does, and a request larger than a slot is accepted. */
+  uint32_t max_chunk_reads;
+  uint32_t reserved[6];
 } grim_server_desc;
 
 typedef struct {
@@ -460,7 +487,8 @@ typedef struct {
   uint64_t device_bytes;    /* device bytes the slots hold                */
   uint64_t submitted, completed, batches, batch_reads, reads_done, records;
   uint64_t overflow_splits; /* merged batches rerun one request at a time */
-  uint64_t queued_requests, queued_reads;
+  uint64_t queued_requests;   /* requests (or chunks of split requests) waiting */
+  uint64_t queued_reads;
   uint64_t cancelled;       /* requests cancelled before they ran         */
 } grim_server_stats;
 

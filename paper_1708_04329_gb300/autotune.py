@@ -11,7 +11,11 @@ reads with CUDA events:
   - the CTA size of the persistent kernel (512, 640 or 768 threads: warps
     per SM against registers per thread);
   - the read tile: KiB of token rows per read range (a range stays in L2
-    while every CTA sweeps its tiles against it).
+    while every CTA sweeps its tiles against it);
+  - how a warp's lane groups take their next reads (each on its own, or
+    all together).
+  A trial replaces the current choice only if it is faster by more than
+  ``min_gain`` (1%): smaller differences are run-to-run noise.
   The paper ties its throughput to the same two widths: how many bins one
   row fetch covers and how many reads share it (§Parameter Evaluation
   Results, parallel width p).
@@ -85,27 +89,30 @@ def _token_bytes(n_reads: int, q: int, max_read_len: int) -> int:
 
 def tune_all_bins(ref, B: int, q: int, max_read_len: int, sample: dict,
                   factors: list[int] | None = None, threads=(512, 640, 768),
-                  ranges_kb=(12 << 10, 24 << 10, 48 << 10, 96 << 10), repeats: int = 2,
+                  ranges_kb=(12 << 10, 24 << 10, 48 << 10, 96 << 10), switches=(1, 2),
+                  repeats: int = 2, min_gain: float = 0.01,
                   cache: Path | None = DEFAULT_CACHE) -> dict:
     """Pick the all-bins mode's tile shapes for reads like `sample`.
 
     ref: uint8 CUDA tensor of the reference; sample: the grim_filter keyword
     arguments (reads, offsets, lens, e) of representative reads, enough to
-    fill the GPU (a few hundred thousand).  Read ranges are only compared
+    fill the GPU (a hundred thousand or more).  Read ranges are only compared
     when the sample's token rows span more than one of them.  Returns
     {"factor": f (0 = one exact pass), "cta_threads": t, "read_range_kb": r,
-    "ms": {trial: ms}}; build the index with grim_build_ex(..., coarse_factor=f,
-    cta_threads=t, read_range_kb=r) and, for f = 0, without the coarse layout.
+    "read_switch": w, "ms": {trial: ms}}; build the index with
+    grim_build_ex(..., coarse_factor=f, cta_threads=t, read_range_kb=r,
+    read_switch=w) and, for f = 0, without the coarse layout.
     """
     n = int(sample["lens"].numel())
     key = (f"allbins|{int(ref.numel())}|{B}|{q}|{max_read_len}|{n}|"
-           f"{tuple(threads)}|{tuple(ranges_kb)}|{_device_name()}")
+           f"{tuple(threads)}|{tuple(ranges_kb)}|{tuple(switches)}|{_device_name()}")
     table = _load(cache)
     if key in table:
         return table[key]
     if factors is None:
         f0 = grim.grim_default_coarse_factor(B, q, max_read_len)
-        factors = [0] + sorted({max(2, f0 // 2), f0, min(64, f0 * 2)})
+        factors = sorted({max(2, f0 // 2), f0, min(64, f0 * 2)})
+        factors = [f0] + [f for f in factors if f != f0] + [0]
     ws = grim.Workspace()
     ms = {}
 
@@ -116,40 +123,54 @@ def tune_all_bins(ref, B: int, q: int, max_read_len: int, sample: dict,
     def run(index):
         return _time(lambda: grim.grim_filter(index, **sample, workspace=ws), repeats)
 
-    # 1. bin tile, at the default launch shape
+    def pick(cur, options, name):
+        """The option to keep: the current one unless another beats it by more
+        than min_gain."""
+        best = cur
+        for o in options:
+            if ms[f"{name}={o}"] < ms[f"{name}={best}"] * (1.0 - min_gain):
+                best = o
+        return best
+
+    # 1. bin tile, at the default launch shape (the first factor is the default)
     for f in factors:
         index = build(f)
         try:
             ms[f"f={f}"] = run(index)
         finally:
             index.close()
-    best_f = min(factors, key=lambda f: ms[f"f={f}"])
+    best_f = pick(factors[0], factors, "f")
     index = build(best_f)
     try:
         d = index.desc
-        best_t, best_r = d.cta_threads, d.read_range_kb
-        base = ms[f"f={best_f}"]
+        best_t, best_r, best_w = d.cta_threads, d.read_range_kb, d.read_switch
+        ms[f"threads={best_t}"] = ms[f"f={best_f}"]
         # 2. CTA size
         for t in threads:
-            if t == best_t:
-                continue
-            grim.grim_index_set_shape(index, t, best_r)
-            ms[f"threads={t}"] = run(index)
-        ms[f"threads={best_t}"] = base
-        best_t = min(threads, key=lambda t: ms[f"threads={t}"])
-        base = ms[f"threads={best_t}"]
-        # 3. read tile: only sizes that split the sample into several ranges
+            if t != best_t:
+                grim.grim_index_set_shape(index, t, best_r, best_w)
+                ms[f"threads={t}"] = run(index)
+        best_t = pick(best_t, threads, "threads")
+        ms[f"switch={best_w}"] = ms[f"threads={best_t}"]
+        # 3. read switch
+        for w in switches:
+            if w != best_w:
+                grim.grim_index_set_shape(index, best_t, best_r, w)
+                ms[f"switch={w}"] = run(index)
+        best_w = pick(best_w, switches, "switch")
+        ms[f"range_kb={best_r}"] = ms[f"switch={best_w}"]
+        # 4. read tile: only sizes that split the sample into several ranges
         tb = _token_bytes(n, q, max_read_len)
         tried = [r for r in ranges_kb if (r << 10) < tb and r != best_r]
         for r in tried:
-            grim.grim_index_set_shape(index, best_t, r)
+            grim.grim_index_set_shape(index, best_t, r, best_w)
             ms[f"range_kb={r}"] = run(index)
-        ms[f"range_kb={best_r}"] = base
-        best_r = min([best_r] + tried, key=lambda r: ms[f"range_kb={r}"])
+        best_r = pick(best_r, tried, "range_kb")
     finally:
         index.close()
     out = {"factor": int(best_f), "cta_threads": int(best_t), "read_range_kb": int(best_r),
-           "ms": {k: round(v, 3) for k, v in ms.items()}, "sample_reads": n}
+           "read_switch": int(best_w), "ms": {k: round(v, 3) for k, v in ms.items()},
+           "sample_reads": n}
     table[key] = out
     _store(cache, table)
     return out

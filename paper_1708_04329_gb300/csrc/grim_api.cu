@@ -298,7 +298,8 @@ int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_
   if (!out) return GRIM_E_ARG;
   *out = nullptr;
   if (!ref || B == 0 || max_read_len < q) return GRIM_E_ARG;
-  if (opts && !exhaustive_shape_ok(opts->cta_threads, opts->read_range_kb)) return GRIM_E_ARG;
+  if (opts && !exhaustive_shape_ok({opts->cta_threads, opts->read_range_kb, opts->read_switch}))
+    return GRIM_E_ARG;
   const uint32_t f = (opts && opts->coarse_factor) ? opts->coarse_factor
                      : (q >= 2 && q <= 6)              ? default_coarse_factor(B, q, max_read_len - 1)
                                                        : 2u;  // q is refused by index_alloc
@@ -306,7 +307,7 @@ int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_
   grim_index* ix = nullptr;
   const int rc = index_alloc(len, B, q, max_read_len, layouts, f, &ix);
   if (rc != GRIM_OK) return rc;
-  if (opts) ix->shape = ExhShape{opts->cta_threads, opts->read_range_kb};
+  if (opts) ix->shape = ExhShape{opts->cta_threads, opts->read_range_kb, opts->read_switch};
   const IndexView& v = ix->v;
   const IndexView& cv = ix->cv;
   const uint64_t bm_bins = cv.num_bins * f;
@@ -423,12 +424,15 @@ int grim_index_info(const grim_index* idx, grim_index_desc* out) {
   out->coarse_factor = idx->factor;
   out->cta_threads = idx->shape.threads ? idx->shape.threads : 640u;
   out->read_range_kb = idx->shape.range_kb ? idx->shape.range_kb : (48u << 10);
+  out->read_switch = idx->shape.read_switch;
   return GRIM_OK;
 }
 
-int grim_index_set_shape(grim_index* idx, uint32_t cta_threads, uint32_t read_range_kb) {
-  if (!idx || !exhaustive_shape_ok(cta_threads, read_range_kb)) return GRIM_E_ARG;
-  idx->shape = ExhShape{cta_threads, read_range_kb};
+int grim_index_set_shape(grim_index* idx, uint32_t cta_threads, uint32_t read_range_kb,
+                         uint32_t read_switch) {
+  const ExhShape s{cta_threads, read_range_kb, read_switch};
+  if (!idx || !exhaustive_shape_ok(s)) return GRIM_E_ARG;
+  idx->shape = s;
   return GRIM_OK;
 }
 
@@ -520,11 +524,17 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
     // otherwise (some read passes almost anywhere) one exact pass
     const uint32_t min_slack = 255u - h.max_tight;
     bool two = capable && (min_slack >= 24 || !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR));
+    // automatic read switch: a warp's lane groups take their next reads
+    // together when every read has as many 16-token blocks (no group waits
+    // long for the others), each on its own otherwise
+    ExhShape shape = idx->shape;
+    if (!shape.read_switch)
+      shape.read_switch = h.blk_max + h.blk_lo == 32u ? GRIM_SWITCH_WARP : GRIM_SWITCH_GROUP;
     if (two) {
       const IndexView& cv = idx->cv;
       const uint32_t cbits = cv.num_bins > 1 ? bit_length(cv.num_bins - 1) : 0;
       launch_exhaustive(cv, rv, ra, cbits, h.max_d, ctl, st, "exhaustive_coarse", {false, 0},
-                        idx->shape);
+                        shape);
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
@@ -553,7 +563,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
     }
     if (two) launch_candidates(v, rv, lists, lists_off, ra, ctl, st, "candidates_refine");
     else launch_exhaustive(v, rv, ra, bin_bits, h.max_d, ctl, st, "exhaustive", {false, 0},
-                           idx->shape);
+                           shape);
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));

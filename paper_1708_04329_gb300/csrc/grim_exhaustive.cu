@@ -42,9 +42,15 @@
 //   it runs on the FMA pipe instead.
 // * Early exit: after each 16-token block the group stops a read once every
 //   one of its 1024 bins is dead -- exact, since a dead bin can never pass.
-// * Groups advance independently (a finished group takes the range's next
-//   read) but stay converged: the per-block work is the same instruction
-//   stream for all four groups, and every warp collective uses the full mask.
+// * Groups stay converged: the per-block work is the same instruction stream
+//   for all groups of a warp, and every warp collective uses the full mask.
+//   Taking a next read (new counters, the claim, the prefetch of the read
+//   after it) runs for the whole warp whenever any group needs it, so the
+//   launch chooses how groups switch reads (WS): each as soon as its read
+//   ends (a switch for every read that ends), or all groups of a warp
+//   together once every one of them has ended (one switch per warp per
+//   round of reads; a group that ends early applies padding tokens, which
+//   change nothing, until the others end).
 #include "grim_internal.cuh"
 
 namespace grim {
@@ -190,7 +196,7 @@ __device__ __forceinline__ void add_block(Counters<P>& c, const uint32_t (&tw)[8
   }
 }
 
-template <int P, int TW, int NT>
+template <int P, int TW, int NT, bool WS>
 __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
   constexpr uint32_t kRowBytes = TW * 4;     // one token's row of a tile
   constexpr uint32_t GL = TW / 4;            // lanes per group (one read)
@@ -353,6 +359,7 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
     switch_reads(true);
     const uint32_t gmask = kGroupMask << (grp * GL);
     bool active = __any_sync(0xFFFFFFFFu, !fin);
+    bool waiting = false;  // WS: the group's read has ended; it waits for the warp's switch
 
     while (active) {
       // (2) one 16-token block for all groups: from the slot, or for the
@@ -360,7 +367,8 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
       {
         uint4 t0, t1;
         const uint32_t bi = nblk - left;  // this read's block index
-        if (TW == 32 || fin || bi < a.slot_blocks) {  // 1024-bin tiles: whole reads in slots
+        // (1024-bin tiles: whole reads in slots; waiting groups read padding)
+        if (TW == 32 || fin || waiting || bi < a.slot_blocks) {
           t0 = lds128(tp);
           t1 = lds128(tp + 16u);
         } else {
@@ -380,9 +388,21 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
       const uint32_t all_dead = c.dead[0] & c.dead[1] & c.dead[2] & c.dead[3];
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, all_dead == ~0u);
       const bool gdead = (bal & gmask) == gmask;
-      const bool done = !fin && (gdead || left == 0);
-      if (__any_sync(0xFFFFFFFFu, done)) {
-        if (done) executed += nblk - left;
+      bool done = !fin && !waiting && (gdead || left == 0);
+      if (WS && done) {
+        // freeze the group's counters (padding adds no misses) until every
+        // group of the warp has ended its read
+        executed += nblk - left;
+        waiting = true;
+        tp = pad_tokens;
+        step = 0;
+      }
+      if (WS ? __all_sync(0xFFFFFFFFu, fin || waiting) : __any_sync(0xFFFFFFFFu, done)) {
+        if (WS) {
+          done = waiting;
+        } else if (done) {
+          executed += nblk - left;
+        }
         const bool emit = done && !gdead;
         if (__any_sync(0xFFFFFFFFu, emit)) {
           uint32_t pm[4], cnt = 0;
@@ -420,6 +440,7 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
         }
         if (done) cur = kNone;
         switch_reads(done);
+        waiting = false;
         active = __any_sync(0xFFFFFFFFu, !fin);
       }
     }
@@ -430,28 +451,35 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
   }
 }
 
-template <int P, int TW, int NT>
+template <int P, int TW, int NT, bool WS>
 void launch_p(const ExhArgs& a, size_t smem, uint32_t threads, uint32_t grid, cudaStream_t st,
               const char* name) {
-  cudaFuncSetAttribute(k_exhaustive<P, TW, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_exhaustive<P, TW, NT, WS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   ProfScope ps(name, st);
-  k_exhaustive<P, TW, NT><<<grid, threads, smem, st>>>(a);
+  k_exhaustive<P, TW, NT, WS><<<grid, threads, smem, st>>>(a);
+}
+
+template <int TW, int NT, bool WS>
+void launch_ws(const ExhArgs& a, size_t smem, uint32_t threads, uint32_t grid, uint32_t max_d,
+               cudaStream_t st, const char* name) {
+  // the counters need 2^P > D' (D' <= 255)
+  if (max_d < 32) launch_p<5, TW, NT, WS>(a, smem, threads, grid, st, name);
+  else if (max_d < 64) launch_p<6, TW, NT, WS>(a, smem, threads, grid, st, name);
+  else if (max_d < 128) launch_p<7, TW, NT, WS>(a, smem, threads, grid, st, name);
+  else launch_p<8, TW, NT, WS>(a, smem, threads, grid, st, name);
 }
 
 template <int TW, int NT>
 void launch_nt(const ExhArgs& a, size_t smem, uint32_t threads, uint32_t grid, uint32_t max_d,
-               cudaStream_t st, const char* name) {
-  // the counters need 2^P > D' (D' <= 255)
-  if (max_d < 32) launch_p<5, TW, NT>(a, smem, threads, grid, st, name);
-  else if (max_d < 64) launch_p<6, TW, NT>(a, smem, threads, grid, st, name);
-  else if (max_d < 128) launch_p<7, TW, NT>(a, smem, threads, grid, st, name);
-  else launch_p<8, TW, NT>(a, smem, threads, grid, st, name);
+               bool warp_switch, cudaStream_t st, const char* name) {
+  if (warp_switch) launch_ws<TW, NT, true>(a, smem, threads, grid, max_d, st, name);
+  else launch_ws<TW, NT, false>(a, smem, threads, grid, max_d, st, name);
 }
 
 template <int TW>
 void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, uint32_t nt,
-               cudaStream_t st, const char* name) {
+               bool warp_switch, cudaStream_t st, const char* name) {
   constexpr uint32_t kRowBytes = TW * 4, GL = TW / 4, kTileBinsT = TW * 32;
   a.n_tiles = (uint32_t)(ix.num_bins_pad / kTileBinsT);
   a.sms = sms;
@@ -471,19 +499,20 @@ void launch_tw(ExhArgs& a, const IndexView& ix, uint32_t max_d, uint32_t sms, ui
     const uint64_t items = (uint64_t)a.n_tiles * ((a.rv.n_reads + per_item - 1) / per_item);
     if (items < grid) grid = (uint32_t)(items ? items : 1);
   }
-  if (nt == 512) launch_nt<TW, 512>(a, smem, threads, grid, max_d, st, name);
-  else if (nt == 768) launch_nt<TW, 768>(a, smem, threads, grid, max_d, st, name);
-  else launch_nt<TW, 640>(a, smem, threads, grid, max_d, st, name);
+  if (nt == 512) launch_nt<TW, 512>(a, smem, threads, grid, max_d, warp_switch, st, name);
+  else if (nt == 768) launch_nt<TW, 768>(a, smem, threads, grid, max_d, warp_switch, st, name);
+  else launch_nt<TW, 640>(a, smem, threads, grid, max_d, warp_switch, st, name);
 }
 
 }  // namespace
 
 uint32_t exhaustive_tile_bins(uint32_t r4) { return r4 <= 1024 ? 32u * 32u : 8u * 32u; }
 
-bool exhaustive_shape_ok(uint32_t threads, uint32_t range_kb) {
-  const bool t_ok = threads == 0 || threads == 512 || threads == 640 || threads == 768;
-  const bool r_ok = range_kb == 0 || (range_kb >= 1024 && range_kb <= (4u << 20));
-  return t_ok && r_ok;
+bool exhaustive_shape_ok(const ExhShape& s) {
+  const bool t_ok = s.threads == 0 || s.threads == 512 || s.threads == 640 || s.threads == 768;
+  const bool r_ok = s.range_kb == 0 || (s.range_kb >= 1024 && s.range_kb <= (4u << 20));
+  const bool w_ok = s.read_switch <= 2;
+  return t_ok && r_ok && w_ok;
 }
 
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
@@ -517,8 +546,9 @@ void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec
   a.range_bytes = shape.range_kb ? (uint64_t)shape.range_kb << 10 : kDefaultRangeBytes;
   a.ctl = ctl;
   const uint32_t nt = shape.threads ? shape.threads : kDefaultThreads;
-  if (ix.r4 <= 1024) launch_tw<32>(a, ix, max_d, (uint32_t)sms, nt, st, prof_name);
-  else launch_tw<8>(a, ix, max_d, (uint32_t)sms, nt, st, prof_name);
+  const bool ws = shape.read_switch == GRIM_SWITCH_WARP;
+  if (ix.r4 <= 1024) launch_tw<32>(a, ix, max_d, (uint32_t)sms, nt, ws, st, prof_name);
+  else launch_tw<8>(a, ix, max_d, (uint32_t)sms, nt, ws, st, prof_name);
 }
 
 }  // namespace grim

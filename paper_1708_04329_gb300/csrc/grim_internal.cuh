@@ -35,7 +35,9 @@ struct Ctl {
   unsigned long long live_bases;   // read bytes in this batch (host-memory plans)
   unsigned long long n_surv;       // survivors of the coarse pass
   unsigned long long n_final;      // passing records of the batch
-  uint32_t pad[46];
+  uint32_t blk_max;                // most 16-token blocks of a read in the batch
+  uint32_t blk_lo;                 // 32 - the fewest 16-token blocks of a read
+  uint32_t pad[44];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte slot");
 static_assert(offsetof(Ctl, live_reads) == 32, "live counts follow the per-pass counters");
@@ -136,19 +138,22 @@ void launch_check_candidates(const uint64_t* cand_off, uint32_t n_reads, uint64_
 // bins per tile of the all-bins kernel for a table of r4 = 4^q rows
 uint32_t exhaustive_tile_bins(uint32_t r4);
 // Launch shape of the all-bins kernel (0 = the default): CTA threads (512,
-// 640 or 768; one persistent CTA per SM) and the token-row bytes of one read
+// 640 or 768; one persistent CTA per SM), the token-row bytes of one read
 // range in KiB (reads are swept range by range so a range's token rows stay
-// in L2 while the CTAs sweep their tiles).
+// in L2 while the CTAs sweep their tiles), and how the lane groups of a warp
+// take their next reads (GRIM_SWITCH_GROUP: each group as its read ends;
+// GRIM_SWITCH_WARP: all groups of the warp together; 0 at launch = GROUP).
 struct ExhShape {
   uint32_t threads;
   uint32_t range_kb;
+  uint32_t read_switch;
 };
-bool exhaustive_shape_ok(uint32_t threads, uint32_t range_kb);
+bool exhaustive_shape_ok(const ExhShape& s);
 // max_d: the batch's largest miss budget (sizes the bit-sliced counters)
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st,
                        const char* prof_name = "exhaustive", Live live = {false, 0},
-                       ExhShape shape = {0, 0});
+                       ExhShape shape = {0, 0, 0});
 // unroll: candidate gathers in flight per lane group (1, 2, 4 or 8; 0 =
 // default).  check_ids: the lists are the caller's; an id outside
 // [0, num_bins) sets kStatusBadCand (and is not gathered).  Internal lists

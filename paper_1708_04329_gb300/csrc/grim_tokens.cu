@@ -162,6 +162,12 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
     const uint32_t tight = 255u - (ntok - d);
     if (tight > *reinterpret_cast<volatile uint32_t*>(&ctl->max_tight))
       atomicMax(&ctl->max_tight, tight);
+    // the spread of the reads' block counts (the all-bins kernel lets a
+    // warp's lane groups switch reads together when every read is as long)
+    const uint32_t nblk = (ntok + kBlockTokens - 1) / kBlockTokens;
+    if (nblk > *reinterpret_cast<volatile uint32_t*>(&ctl->blk_max)) atomicMax(&ctl->blk_max, nblk);
+    if (32u - nblk > *reinterpret_cast<volatile uint32_t*>(&ctl->blk_lo))
+      atomicMax(&ctl->blk_lo, 32u - nblk);
   }
 }
 

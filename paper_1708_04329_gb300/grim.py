@@ -33,6 +33,8 @@ GRIM_E_IO = -14
 GRIM_E_FORMAT = -15
 GRIM_E_CANCELLED = -16
 GRIM_LOAD_VERIFY = 1
+GRIM_SWITCH_GROUP = 1
+GRIM_SWITCH_WARP = 2
 GRIM_PLAN_CANDIDATES = 1
 GRIM_PLAN_HOST_IO = 2
 
@@ -75,7 +77,8 @@ class _Desc(C.Structure):
                 ("bin_major_bytes", C.c_uint64), ("coarse_token_major", C.c_void_p),
                 ("num_coarse", C.c_uint64), ("num_coarse_pad", C.c_uint64),
                 ("coarse_token_major_bytes", C.c_uint64), ("coarse_factor", C.c_uint32),
-                ("cta_threads", C.c_uint32), ("read_range_kb", C.c_uint32)]
+                ("cta_threads", C.c_uint32), ("read_range_kb", C.c_uint32),
+                ("read_switch", C.c_uint32)]
 
 
 class _Stats(C.Structure):
@@ -86,7 +89,8 @@ class _Stats(C.Structure):
 
 class _BuildOpts(C.Structure):
     _fields_ = [("coarse_factor", C.c_uint32), ("cta_threads", C.c_uint32),
-                ("read_range_kb", C.c_uint32), ("reserved", C.c_uint32 * 5)]
+                ("read_range_kb", C.c_uint32), ("read_switch", C.c_uint32),
+                ("reserved", C.c_uint32 * 4)]
 
 
 class _PlanDesc(C.Structure):
@@ -105,7 +109,7 @@ class _ServerDesc(C.Structure):
                 ("max_cand", C.c_uint64), ("cap", C.c_uint64), ("max_e", C.c_uint32),
                 ("flags", C.c_uint32), ("mem_budget", C.c_uint64),
                 ("max_queued_reads", C.c_uint64), ("cand_unroll", C.c_uint32),
-                ("reserved", C.c_uint32 * 7)]
+                ("max_chunk_reads", C.c_uint32), ("reserved", C.c_uint32 * 6)]
 
 
 class _RequestInfo(C.Structure):
@@ -155,7 +159,7 @@ def _lib() -> C.CDLL:
         lib.grim_index_info.restype = i32
         lib.grim_index_info.argtypes = [vp, C.POINTER(_Desc)]
         lib.grim_index_set_shape.restype = i32
-        lib.grim_index_set_shape.argtypes = [vp, u32, u32]
+        lib.grim_index_set_shape.argtypes = [vp, u32, u32, u32]
         lib.grim_free.restype = None
         lib.grim_free.argtypes = [vp]
         lib.grim_strerror.restype = C.c_char_p
@@ -331,6 +335,7 @@ class IndexDesc:
     coarse_factor: int = 0
     cta_threads: int = 0
     read_range_kb: int = 0
+    read_switch: int = 0
 
 
 class GrimIndex:
@@ -418,11 +423,11 @@ def grim_build_host(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_
 
 def grim_build_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
                   coarse_factor: int = 0, stream=None, cta_threads: int = 0,
-                  read_range_kb: int = 0) -> GrimIndex:
+                  read_range_kb: int = 0, read_switch: int = 0) -> GrimIndex:
     """grim_build_ex: grim_build with build options (``coarse_factor``: bins per
     super-bin of the coarse table; ``cta_threads``, ``read_range_kb``: the
     all-bins kernel's launch shape; 0 = the library default)."""
-    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb)
+    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb, read_switch)
     h = C.c_void_p()
     rc = _lib().grim_build_ex(_dptr(ref, "ref", 1), ref.numel(), B, q, max_read_len, layouts,
                               C.byref(opts), _stream_ptr(stream), C.byref(h))
@@ -433,11 +438,11 @@ def grim_build_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LA
 
 def grim_build_host_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
                        coarse_factor: int = 0, stream=None, cta_threads: int = 0,
-                       read_range_kb: int = 0) -> GrimIndex:
+                       read_range_kb: int = 0, read_switch: int = 0) -> GrimIndex:
     """grim_build_host_ex: grim_build_host with build options."""
     p, keep = _hptr(ref, "ref", np.uint8)
     n = keep.numel() if hasattr(keep, "numel") else keep.size
-    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb)
+    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb, read_switch)
     h = C.c_void_p()
     rc = _lib().grim_build_host_ex(p, n, B, q, max_read_len, layouts, C.byref(opts),
                                    _stream_ptr(stream), C.byref(h))
@@ -521,14 +526,16 @@ def grim_index_info(index: GrimIndex) -> IndexDesc:
                      d.layouts, d.words_per_bin, d.token_major or 0, d.bin_major or 0,
                      d.token_major_bytes, d.bin_major_bytes, d.coarse_token_major or 0,
                      d.num_coarse, d.num_coarse_pad, d.coarse_token_major_bytes, d.coarse_factor,
-                     d.cta_threads, d.read_range_kb)
+                     d.cta_threads, d.read_range_kb, d.read_switch)
 
 
-def grim_index_set_shape(index: GrimIndex, cta_threads: int = 0, read_range_kb: int = 0) -> None:
+def grim_index_set_shape(index: GrimIndex, cta_threads: int = 0, read_range_kb: int = 0,
+                         read_switch: int = 0) -> None:
     """Launch shape of the all-bins kernel for later calls with this index:
-    CTA threads (512, 640 or 768) and the read tile in KiB of token rows per
-    read range; 0 restores a default."""
-    rc = _lib().grim_index_set_shape(index.handle, cta_threads, read_range_kb)
+    CTA threads (512, 640 or 768), the read tile in KiB of token rows per
+    read range, and GRIM_SWITCH_GROUP / GRIM_SWITCH_WARP; 0 restores a
+    default."""
+    rc = _lib().grim_index_set_shape(index.handle, cta_threads, read_range_kb, read_switch)
     if rc != GRIM_OK:
         raise GrimError(rc, "grim_index_set_shape")
 
@@ -990,10 +997,12 @@ class GrimServer:
 def grim_server_create(index: GrimIndex, slots: int, max_reads: int, max_bases: int, max_e: int,
                        cap: int, max_cand: int = 0, candidates: bool = False,
                        mem_budget: int = 0, max_queued_reads: int = 0,
-                       cand_unroll: int = 0) -> GrimServer:
+                       cand_unroll: int = 0, max_chunk_reads: int = 0) -> GrimServer:
+    """``max_chunk_reads``: cut requests into chunks of at most this many
+    consecutive reads (0: run each request whole)."""
     d = _ServerDesc(slots, max_reads, max_bases, max_cand, cap, max_e,
                     GRIM_PLAN_CANDIDATES if candidates else 0, mem_budget, max_queued_reads,
-                    cand_unroll)
+                    cand_unroll, max_chunk_reads)
     h = C.c_void_p()
     rc = _lib().grim_server_create(index.handle, C.byref(d), C.byref(h))
     if rc != GRIM_OK:

@@ -50,11 +50,13 @@ def test_every_launch_shape_matches_oracle(world):
         # 1 MiB ranges split the 6000 reads' 1.5 MB of token rows in two
         for threads in (512, 640, 768):
             for range_kb in (1024, 0):
-                grim.grim_index_set_shape(idx, threads, range_kb)
-                assert_same(_host(grim.grim_filter(idx, **kw)), want)
+                for switch in (0, grim.GRIM_SWITCH_GROUP, grim.GRIM_SWITCH_WARP):
+                    grim.grim_index_set_shape(idx, threads, range_kb, switch)
+                    assert_same(_host(grim.grim_filter(idx, **kw)), want)
         grim.grim_index_set_shape(idx)  # defaults
-        assert (idx.desc.cta_threads, idx.desc.read_range_kb) == (640, 48 << 10)
-        for bad in ((600, 0), (0, 512), (0, (4 << 20) + 1)):
+        d = idx.desc
+        assert (d.cta_threads, d.read_range_kb, d.read_switch) == (640, 48 << 10, 0)
+        for bad in ((600, 0, 0), (0, 512, 0), (0, (4 << 20) + 1, 0), (0, 0, 3)):
             with pytest.raises(grim.GrimError) as ei:
                 grim.grim_index_set_shape(idx, *bad)
             assert ei.value.code == grim.GRIM_E_ARG
@@ -71,11 +73,12 @@ def test_tuned_shape_matches_oracle(world):
                                    cache=None)
     f0 = grim.grim_default_coarse_factor(200, 5, 250)
     assert set(tuned["ms"]) >= {"f=0", f"f={f0}", "threads=512", "threads=640", "threads=768",
-                                "range_kb=1024"}
+                                "range_kb=1024", "switch=1", "switch=2"}
     assert tuned["factor"] in (0, max(2, f0 // 2), f0, f0 * 2)
     layouts = grim.GRIM_LAYOUT_BOTH if tuned["factor"] == 0 else grim.GRIM_LAYOUT_ALL
     idx = grim.grim_build_ex(ref, 200, 5, 250, layouts, tuned["factor"],
-                             cta_threads=tuned["cta_threads"], read_range_kb=tuned["read_range_kb"])
+                             cta_threads=tuned["cta_threads"], read_range_kb=tuned["read_range_kb"],
+                             read_switch=tuned["read_switch"])
     assert_same(_host(grim.grim_filter(idx, **kw)), want)
     # and through a graph-captured plan, which takes the index's shape when created
     plan = grim.grim_plan_create(idx, max_reads=rs.n, max_bases=len(rs.seq), max_e=int(rs.e.max()),

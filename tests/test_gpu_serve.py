@@ -260,3 +260,77 @@ def test_server_cancel(world):
     st = srv.stats()
     assert st["cancelled"] == 1 and st["completed"] == 39
     srv.close()
+
+
+def test_server_chunked_requests(world):
+    """With max_chunk_reads, requests are cut into chunks of consecutive reads
+    that run in different batches and slots; each request's result -- one
+    larger than a slot among them, and an 8,192-read one among small ones --
+    equals the request filtered alone and the oracle."""
+    from paper_1708_04329_gb300 import grim
+
+    g, oix, idx = world
+    srv = grim.grim_server_create(idx, slots=3, max_reads=1024, max_bases=1024 * 250, max_e=12,
+                                  cap=60_000, max_chunk_reads=256)
+    sizes = [8192, 1, 40, 700, 2000, 3, 257, 256, 90]
+    reqs = _requests(g, sizes, 1200)
+    tickets = [srv.submit(**_host_args(rs)) for rs in reqs]
+    results = [srv.result(t, timeout_s=120) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["reads_done"] == sum(sizes)
+    # the 8,192-read request alone needed 8 batches of 1,024 reads (32 chunks)
+    assert st["batches"] >= 8
+    for rs, (got, info) in zip(reqs, results):
+        assert info.status == 0 and info.n_reads == rs.n
+        assert_same(got, grim.grim_filter_host(idx, **_host_args(rs), cap=400_000))
+    for rs, (got, _) in list(zip(reqs, results))[1:5]:
+        assert_same(got, oracle.filter(oix, rs))
+
+
+def test_server_chunked_candidates_cancel_overflow(world):
+    """Chunks also split on the candidate limit; a chunked request can be
+    cancelled while all its chunks wait; a chunk over the capacity fails its
+    request with GRIM_E_OVERFLOW and the request's total."""
+    from paper_1708_04329_gb300 import grim, synth
+
+    g, oix, idx = world
+    srv = grim.grim_server_create(idx, slots=2, max_reads=300, max_bases=300 * 250, max_e=12,
+                                  cap=40_000, max_cand=3000, candidates=True, max_chunk_reads=300)
+    rs = _ragged(g, 900, 1300)
+    off, cand = synth.candidates((rs.true_pos // 200).astype(np.int32), oix.num_bins, seed=1300,
+                                 median=25)
+    assert off[-1] > 3000  # more candidates than one batch holds
+    got, info = srv.result(srv.submit(**_host_args(rs), cand=cand, cand_off=off), timeout_s=120)
+    assert_same(got, oracle.filter(oix, rs, cand_off=off, cand=cand))
+    srv.close()
+
+    # one slot of 20 reads; the last request's chunks wait behind 30 others
+    srv = grim.grim_server_create(idx, slots=1, max_reads=20, max_bases=20 * 250, max_e=12,
+                                  cap=20_000, max_chunk_reads=10)
+    reqs = _requests(g, [20] * 30 + [55], 1400)
+    ts = [srv.submit(**_host_args(r)) for r in reqs]
+    assert srv.cancel(ts[-1]) is True
+    with pytest.raises(grim.GrimError) as ei:
+        srv.result(ts[-1], timeout_s=60)
+    assert ei.value.code == grim.GRIM_E_CANCELLED
+    for t, r in list(zip(ts, reqs))[:-1]:
+        got, _ = srv.result(t, timeout_s=60)
+        assert_same(got, oracle.filter(oix, r))
+    srv.close()
+
+    big = _ragged(g, 400, 1500)
+    want = oracle.filter(oix, big)
+    per_chunk = max(len(oracle.filter(oix, big.subset(range(k, min(k + 50, 400))))[0])
+                    for k in range(0, 400, 50))
+    srv = grim.grim_server_create(idx, slots=2, max_reads=100, max_bases=100 * 250, max_e=12,
+                                  cap=per_chunk // 2, max_chunk_reads=50)
+    with pytest.raises(grim.GrimError) as ei:
+        srv.result(srv.submit(**_host_args(big)), timeout_s=60)
+    assert ei.value.code == grim.GRIM_E_OVERFLOW
+    assert ei.value.n_out == len(want[0])
+    srv.close()
+    with pytest.raises(grim.GrimError) as ei:  # a chunk larger than a batch
+        grim.grim_server_create(idx, slots=1, max_reads=10, max_bases=2500, max_e=12, cap=100,
+                                max_chunk_reads=11)
+    assert ei.value.code == grim.GRIM_E_ARG
