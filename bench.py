@@ -48,7 +48,20 @@ UNIT = "reads/s"
 # measured again, and so does any run at other than the default sizes.  The
 # figures come from one-launch ncu captures of small cases of the same
 # workloads, scaled to the full launch by the rule each entry states.
-TRAFFIC = {}
+TRAFFIC = {
+    # all-bins kernel, 1M reads of 100 bp (4 read ranges), linear in the
+    # tiles swept: captures at 0.4 and 0.8 Gbp (977 and 1,954 coarse tiles:
+    # 1.298 and 2.191 GB per launch) give 0.405 GB + 0.914 MB per tile;
+    # 7,569 coarse tiles of the 3.1 Gbp table
+    ("9746ed514f533e03", "human:exhaustive_coarse"): 7_321_903_209,
+    # the same rule for the one exact pass over bins (1,954 and 3,907 tiles:
+    # 2.031 and 3.685 GB; 0.376 GB + 0.847 MB per tile); 15,137 tiles
+    ("9746ed514f533e03", "human:exhaustive_exact"): 13_193_542_521,
+    # candidate kernel, in proportion to the pairs gathered: the 3.1 Gbp
+    # bin-major table (1.98 GB, as at full size) with 100k ragged reads,
+    # 32,876,582 pairs, 4.314 GB (131.2 B per pair); 1,320,234,389 pairs
+    ("0b88d3370894bf47", "ragged:candidates"): 173_256_211_892,
+}
 
 
 DEFAULT_GENOME, DEFAULT_READS = 3_100_000_000, 1_000_000
@@ -95,6 +108,8 @@ def parse_args():
                    help="reads of the batch the all-bins autotuner times its trials on")
     p.add_argument("--no-legs", action="store_true",
                    help="headline only: skip the one-pass exact, ragged and finer-index legs")
+    p.add_argument("--legs", default="exact,ragged,finer",
+                   help="which legs the headline line carries (comma-separated)")
     p.add_argument("--genome", type=int, default=DEFAULT_GENOME, help="reference length (bases)")
     p.add_argument("--reads", type=int, default=DEFAULT_READS, help="reads per rank")
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -451,14 +466,17 @@ def run_native(args, rank, world, local):
         line["e2e"] = run_e2e(args, w, st, shape)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
-    legs = rank == 0 and world == 1 and args.workload == "human" and not args.no_legs
-    if legs:
+    legs = set()
+    if rank == 0 and world == 1 and args.workload == "human" and not args.no_legs:
+        legs = {x.strip() for x in args.legs.split(",") if x.strip()}
+    if "exact" in legs:
         line["exact_one_pass"] = exact_leg(w, dev, ref, shape, st, n_sm, sm_max, args)
     del dev, cand, cand_off, ref, outs, ws
     torch.cuda.empty_cache()
-    if legs:
+    if "ragged" in legs:
         line["ragged"] = ragged_leg(args, w["genome"])
         torch.cuda.empty_cache()
+    if "finer" in legs:
         line["finer"] = finer_leg(args, w["genome"], n_sm, sm_max, peaks)
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_serve:

@@ -498,6 +498,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
   launch_tokenise(reads, offsets, lens, e, v, rv, tokens, meta, ctl, st);
   if (cand_mode) launch_check_candidates(cand_off, n_reads, n_cand, ctl, st);
+  else if (!idx->shape.read_switch) launch_block_spread(lens, n_reads, v.q, ctl, st);
   CK(cudaGetLastError());
   // input errors end the call before the filter runs; the batch's largest
   // miss budget sizes the all-bins kernel's counters

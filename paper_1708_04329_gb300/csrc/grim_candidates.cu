@@ -17,8 +17,9 @@
 // * A bin vector (4^q bits) is gathered by G lanes with 16-byte loads
 //   (q = 5: 8 lanes x 16 B = 128 B, four candidates per warp step; q = 6:
 //   32 lanes x 16 B = 512 B).  The U vectors of a step are reduced over the
-//   lane group together (a butterfly that halves the sums at each exchange),
-//   compared with T = (L-q+1) - q*e, and one ballot places the passes.
+//   lane group together (a butterfly that halves the sums at each exchange;
+//   for a whole-warp group, one redux.sync per vector), compared with
+//   T = (L-q+1) - q*e, and one ballot places the passes.
 // * The path is a random 128/512-byte gather per (read, bin) pair: bound by
 //   HBM, not by arithmetic.
 #include "grim_internal.cuh"
@@ -397,7 +398,19 @@ __global__ void __launch_bounds__(kWarps * 32, cand_ctas_per_sm(WPB)) k_candidat
             sums[u] = off + u * CPW + slot < n ? plane_sum<WPB, WL>(v[u], P, K, xplanes, sub, nh) : 0u;
           // bins past num_bins exist only as zero padding of the table
           // (members of the last super-bin); they never pass
-          if constexpr (U > 1 && U <= G) {
+          if constexpr (G == 32) {
+            // a lane group is the whole warp (512-byte vectors): one
+            // full-warp reduction per candidate, and lane u emits candidate u
+            uint32_t total = 0, id = 0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+              const uint32_t t = __reduce_add_sync(0xFFFFFFFFu, sums[u]);
+              total = lane == (uint32_t)u ? t : total;
+              id = lane == (uint32_t)u ? bc[u] : id;
+            }
+            const uint32_t c = off + lane;
+            emit(lane < (uint32_t)U && c < n && id < num_bins && total >= thr, c, total);
+          } else if constexpr (U > 1 && U <= G) {
             // the U sums reduced over the lane group at once: each lane ends
             // with the total of candidate uq, held by G/U lanes
             const uint32_t total = reduce_scatter<G, U>(sums, sub);

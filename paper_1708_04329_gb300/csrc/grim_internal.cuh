@@ -129,6 +129,10 @@ void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t*
                      const uint16_t* e, const IndexView& ix, ReadsView rv, uint16_t* tokens,
                      uint32_t* meta, Ctl* ctl, cudaStream_t st, Live live = {false, 0},
                      uint32_t max_e = 0xFFFFu, uint64_t max_bases = ~0ull);
+// ctl->blk_max / blk_lo: the most 16-token blocks of a read of the batch, and
+// 32 - the fewest
+void launch_block_spread(const uint32_t* lens, uint32_t n_reads, uint32_t q, Ctl* ctl,
+                         cudaStream_t st);
 // CSR offsets of the caller's lists: non-decreasing, ending at n_cand
 // (kStatusBadCsr otherwise); the ids themselves are checked by the
 // candidate kernel

@@ -162,12 +162,30 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
     const uint32_t tight = 255u - (ntok - d);
     if (tight > *reinterpret_cast<volatile uint32_t*>(&ctl->max_tight))
       atomicMax(&ctl->max_tight, tight);
-    // the spread of the reads' block counts (the all-bins kernel lets a
-    // warp's lane groups switch reads together when every read is as long)
+  }
+}
+
+// The spread of the reads' 16-token block counts (ctl->blk_max, blk_lo =
+// 32 - the fewest): the all-bins kernel can let a warp's lane groups take
+// their next reads together when every read spans as many blocks.  Reads
+// shorter than q are left out (the tokeniser fails the batch for them).
+__global__ void k_block_spread(const uint32_t* __restrict__ lens, uint32_t n_reads, uint32_t q,
+                               Ctl* ctl) {
+  uint32_t hi = 0, lo = 0;  // most blocks, 32 - fewest blocks
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_reads;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t L = lens[i];
+    if (L < q) continue;
+    const uint32_t ntok = min(L - q + 1, kMaxTokens);
     const uint32_t nblk = (ntok + kBlockTokens - 1) / kBlockTokens;
-    if (nblk > *reinterpret_cast<volatile uint32_t*>(&ctl->blk_max)) atomicMax(&ctl->blk_max, nblk);
-    if (32u - nblk > *reinterpret_cast<volatile uint32_t*>(&ctl->blk_lo))
-      atomicMax(&ctl->blk_lo, 32u - nblk);
+    hi = max(hi, nblk);
+    lo = max(lo, 32u - nblk);
+  }
+  hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+  lo = __reduce_max_sync(0xFFFFFFFFu, lo);
+  if ((threadIdx.x & 31) == 0) {
+    if (hi) atomicMax(&ctl->blk_max, hi);
+    if (lo) atomicMax(&ctl->blk_lo, lo);
   }
 }
 
@@ -227,6 +245,19 @@ void launch_tokenise(const char* reads, const uint64_t* offsets, const uint32_t*
   k_tokenise<<<(unsigned)grid, threads, 0, st>>>(reads, offsets, lens, e, rv.n_reads, ix.q,
                                                  ix.max_read_len, ix.r4, rv.ts, ix.presence, tokens,
                                                  meta, ctl, live, max_e, max_bases, copies);
+}
+
+void launch_block_spread(const uint32_t* lens, uint32_t n_reads, uint32_t q, Ctl* ctl,
+                         cudaStream_t st) {
+  if (n_reads == 0) return;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t need = ((uint64_t)n_reads + 255) / 256;
+  const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * 4;
+  const uint32_t grid = (uint32_t)(need < cap ? need : cap);
+  ProfScope ps("block_spread", st);
+  k_block_spread<<<grid, 256, 0, st>>>(lens, n_reads, q, ctl);
 }
 
 void launch_check_candidates(const uint64_t* cand_off, uint32_t n_reads, uint64_t n_cand, Ctl* ctl,
