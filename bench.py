@@ -61,6 +61,10 @@ TRAFFIC = {
     # bin-major table (1.98 GB, as at full size) with 100k ragged reads,
     # 32,876,582 pairs, 4.314 GB (131.2 B per pair); 1,320,234,389 pairs
     ("0b88d3370894bf47", "ragged:candidates"): 173_256_211_892,
+    # the same rule at q = 6: 0.4 Gbp (a 2 GB table, 6.4% L2 hits against
+    # ~1% on the full 15.9 GB one, so this is low by up to ~5%), 6,565,154
+    # pairs, 3.260 GB (496.6 B per pair); 329,738,997 pairs
+    ("0b88d3370894bf47", "finer:candidates"): 163_736_639_321,
 }
 
 
