@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from tests.conftest import Reads, load_fixture, random_case
-from tests.gpu_helpers import assert_same, build, gpu_filter
+from tests.gpu_helpers import assert_same, build, dev_reads, gpu_filter
 
 pytestmark = pytest.mark.gpu
 
@@ -405,3 +405,50 @@ def test_degenerate_genome_and_reads(layouts):
             cand = np.array([0, 1, nb - 1, 5, 4, 3, 2, 0, nb - 1, 7, 8, 9], np.int32)
             assert_same(gpu_filter(idx, rs, off, cand), oracle.filter(oix, rs, cand_off=off, cand=cand))
         idx.close()
+
+
+def test_filter_stats_are_per_thread():
+    """grim_last_filter_stats reports the calling thread's own last call:
+    two threads filtering different batches at the same time (each on its
+    own stream and workspace) each read back the counters of their own call,
+    identical to the same call made alone."""
+    import threading
+
+    from paper_1708_04329_gb300 import grim, synth
+
+    torch.cuda.set_device(0)
+    g = synth.human_genome(1_500_000, seed=91)
+    idx = build(g, 200, 5, 100)
+    batches = [synth.reads(g, 3000, seed=92, e=5, max_edits=5),
+               synth.reads(g, 1200, seed=93, e=3, max_edits=3)]
+    alone = []
+    for rs in batches:
+        grim.grim_filter(idx, **dev_reads(rs))
+        alone.append(grim.grim_last_filter_stats())
+    assert alone[0] != alone[1]
+    got = [None, None]
+    errors = []
+
+    def work(i):
+        try:
+            st = torch.cuda.Stream()
+            ws = grim.Workspace()
+            kw = dev_reads(batches[i])
+            for _ in range(5):
+                with torch.cuda.stream(st):
+                    grim.grim_filter(idx, **kw, workspace=ws, stream=st)
+                s = grim.grim_last_filter_stats()
+                if s != alone[i]:
+                    errors.append((i, s))
+            got[i] = s
+        except Exception as e:  # surfaced below
+            errors.append((i, repr(e)))
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert got == alone
+    idx.close()
