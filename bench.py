@@ -96,6 +96,11 @@ def parse_args():
                    help="ragged workload: candidate gathers in flight (0 = autotune)")
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="serve workload: length of the measured arrival trace")
+    p.add_argument("--serve-rate", type=float, default=0.0,
+                   help="serve workload: offered batches/s of the measured trace (0: the "
+                        "highest stable rate of the sweep)")
+    p.add_argument("--serve-path", type=int, default=0,
+                   help="serve workload: all-bins path (0 automatic, 1 two-level, 2 one exact pass)")
     p.add_argument("--serve-chunk", type=int, default=0,
                    help="serve workload: cut requests into chunks of at most this many reads "
                         "(0: whole requests)")
@@ -318,18 +323,19 @@ def sample_of(dev: dict, rs, n: int) -> dict:
 def all_bins_shape(args, w, dev, ref) -> dict:
     """The all-bins tile shapes of this workload: the autotuner's pick, timed on
     the batch's first --tune-reads reads, unless --coarse-factor or --no-tune
-    fixes them.  `layouts` drops the coarse table when one exact pass wins."""
+    fixes them."""
     from paper_1708_04329_gb300 import autotune, grim
 
     if args.coarse_factor or args.no_tune:
-        return {"tuned": False, "factor": args.coarse_factor, "cta_threads": 0,
-                "read_range_kb": 0, "read_switch": 0, "layouts": grim.GRIM_LAYOUT_ALL}
+        return {"tuned": False, "factor": args.coarse_factor, "all_bins_path": 0,
+                "cta_threads": 0, "read_range_kb": 0, "read_switch": 0,
+                "layouts": grim.GRIM_LAYOUT_ALL}
     t0 = time.perf_counter()
     out = autotune.tune_all_bins(ref, w["B"], w["q"], w["max_read_len"],
                                  sample_of(dev, w["reads"], args.tune_reads), repeats=1,
                                  cache=None)
     out = dict(out, tuned=True, tune_s=round(time.perf_counter() - t0, 1))
-    out["layouts"] = grim.GRIM_LAYOUT_ALL if out["factor"] else grim.GRIM_LAYOUT_BOTH
+    out["layouts"] = grim.GRIM_LAYOUT_ALL
     return out
 
 
@@ -377,7 +383,8 @@ def run_native(args, rank, world, local):
         idx = grim.grim_build_ex(ref, B, q, mrl, shape["layouts"], shape["factor"], stream=st,
                                  cta_threads=shape["cta_threads"],
                                  read_range_kb=shape["read_range_kb"],
-                                 read_switch=shape["read_switch"])
+                                 read_switch=shape["read_switch"],
+                                 all_bins_path=shape["all_bins_path"])
         evs[1].record(st)
         a = grim.grim_filter(idx, **dev, out=outs[0], workspace=ws, stream=st)
         evs[2].record(st)
@@ -664,7 +671,8 @@ def run_e2e(args, w, st, shape):
                                       shape["layouts"], shape["factor"], stream=st,
                                       cta_threads=shape["cta_threads"],
                                       read_range_kb=shape["read_range_kb"],
-                                      read_switch=shape["read_switch"])
+                                      read_switch=shape["read_switch"],
+                                      all_bins_path=shape["all_bins_path"])
         t.append(time.perf_counter())
         a = grim.grim_filter_host(idx, h["seq"], h["off"], h["lens"], h["e"], out=outs[0], stream=st)
         t.append(time.perf_counter())
@@ -960,6 +968,7 @@ def _serve_trace(srv, rs, trace, paced: bool, max_outstanding: int = 1 << 17,
 
     q = queue.Queue()
     lat, reads_done, merged = [], [0], []
+    wait, run, breads = [], [], []
     outstanding = [0]
     cv = threading.Condition()
 
@@ -972,6 +981,9 @@ def _serve_trace(srv, rs, trace, paced: bool, max_outstanding: int = 1 << 17,
             (r, _b, _c), info = srv.result(ticket)
             lat.append(info.t_done_ns - target)
             merged.append(info.batch_requests)
+            wait.append(info.t_launch_ns - info.t_submit_ns)
+            run.append(info.t_done_ns - info.t_launch_ns)
+            breads.append(info.batch_reads)
             reads_done[0] += n
             with cv:
                 outstanding[0] -= n
@@ -1013,6 +1025,13 @@ def _serve_trace(srv, rs, trace, paced: bool, max_outstanding: int = 1 << 17,
             "p999_ms": float(np.percentile(lat_ms, 99.9)) if len(lat) else None,
             "max_ms": float(lat_ms.max()) if len(lat) else None,
             "mean_requests_per_batch": float(np.mean(merged)) if merged else None,
+            # where a request's time goes: waiting for a slot (submission to
+            # launch of its batch) and its batch's run on the GPU
+            "queue_wait_ms": ({k: float(np.percentile(np.array(wait) / 1e6, p))
+                               for k, p in (("p50", 50), ("p99", 99))} if wait else None),
+            "batch_run_ms": ({k: float(np.percentile(np.array(run) / 1e6, p))
+                              for k, p in (("p50", 50), ("p99", 99))} if run else None),
+            "batch_reads_p50": float(np.percentile(breads, 50)) if breads else None,
             "submit_lag_p99_ms": float(np.percentile(np.array(lag) / 1e6, 99)) if lag else None}
 
 
@@ -1078,6 +1097,7 @@ def serving_leg(g, trace_s: float = 10.0, load: float = 0.85) -> dict:
             "latency_ms": {k: round(main[k + "_ms"], 2) for k in ("p50", "p99", "p999")},
             "capacity_reads_per_s": round(cap_run["reads_per_s"], 1),
             "mean_requests_per_batch": round(main["mean_requests_per_batch"], 2),
+            "queue_wait_ms": main["queue_wait_ms"], "batch_run_ms": main["batch_run_ms"],
             "trace": (f"{trace_s:.0f} s Poisson trace, {main['requests']} requests, sizes "
                       "log-uniform 1..8192, L in {100,150,250}, e <= 0.05 L; 3 slots; "
                       "bench.py --workload serve runs the full 60 s measurement")}
@@ -1101,7 +1121,8 @@ def run_serve(args, rank, world, local):
     rs = w["reads"]
     gen_s = time.perf_counter() - t0
     ref = torch.from_numpy(w["genome"]).cuda()
-    idx = grim.grim_build(ref, w["B"], w["q"], w["max_read_len"], grim.GRIM_LAYOUT_ALL)
+    idx = grim.grim_build_ex(ref, w["B"], w["q"], w["max_read_len"], grim.GRIM_LAYOUT_ALL,
+                             all_bins_path=args.serve_path)
     del ref
     torch.cuda.synchronize()
     slot_reads = 16384
@@ -1125,6 +1146,8 @@ def run_serve(args, rank, world, local):
             best = rate
     if best is None:
         best = 0.5 * capacity
+    if args.serve_rate > 0:
+        best = args.serve_rate
     trace = synth.request_trace(args.serve_seconds, best, rs.n, seed=63)
     props = torch.cuda.get_device_properties(local)
     uuid = getattr(props, "uuid", None)
@@ -1157,6 +1180,9 @@ def run_serve(args, rank, world, local):
                    "l2": "table (1.98 GB) larger than L2"},
         "offered_batches_per_s": round(best, 1),
         "latency_ms": {k: round(main[k + "_ms"], 3) for k in ("p50", "p99", "p999", "max")},
+        "queue_wait_ms": main["queue_wait_ms"], "batch_run_ms": main["batch_run_ms"],
+        "batch_reads_p50": main["batch_reads_p50"],
+        "all_bins_path": "two-level" if idx.desc.two_level else "one exact pass",
         "drain_s": round(main["drain_s"], 3),
         "mean_requests_per_batch": round(main["mean_requests_per_batch"], 2),
         "capacity_reads_per_s": round(cap_run["reads_per_s"], 1),

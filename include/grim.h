@@ -103,6 +103,9 @@ typedef struct {
   uint32_t cta_threads;      /* threads of its one persistent CTA per SM        */
   uint32_t read_range_kb;    /* token-row KiB of one read range (the read tile) */
   uint32_t read_switch;      /* GRIM_SWITCH_GROUP, GRIM_SWITCH_WARP, 0 = automatic */
+  uint32_t all_bins_path;    /* GRIM_PATH_* as set (0 = automatic)              */
+  uint32_t two_level;        /* 1: all-bins calls take coarse-then-exact (before
+                                the per-batch rules), 0: one exact pass         */
 } grim_index_desc;
 
 /*
@@ -129,9 +132,19 @@ int grim_build_host(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint3
                     uint32_t layouts, void* stream, grim_index** out);
 
 /* How the lane groups of a warp in the all-bins kernel take their next read
- * (grim_index_set_shape). */
+ * (grim_shape). */
 #define GRIM_SWITCH_GROUP 1u /* each group as soon as its read ends             */
 #define GRIM_SWITCH_WARP 2u  /* all groups of a warp together, once all ended   */
+
+/* The all-bins path (grim_shape).  Automatic (0): coarse-then-exact when the
+ * index has the coarse and bin-major tables and its super-bin window would
+ * hold at most 40% of the 4^q tokens in a uniform random sequence (denser
+ * coarse tables let too many super-bins pass: at q = 5, B = 200 that is
+ * reads up to about 200 bp), else one exact pass; a batch whose tightest
+ * read has fewer than 24 tokens of slack takes the exact pass too.  An
+ * index with only one of the two paths' tables always takes that path. */
+#define GRIM_PATH_TWO_LEVEL 1u /* coarse pass over super-bins, then exact checks */
+#define GRIM_PATH_EXACT 2u     /* one exact pass over every bin                  */
 
 /* Build options.  Zero-initialise and set what you need. */
 typedef struct {
@@ -147,8 +160,9 @@ typedef struct {
    * in KiB of token rows per read range (1024 .. 4194304). */
   uint32_t cta_threads;
   uint32_t read_range_kb;
-  uint32_t read_switch;  /* GRIM_SWITCH_* (0 = automatic) */
-  uint32_t reserved[4];
+  uint32_t read_switch;    /* GRIM_SWITCH_* (0 = automatic) */
+  uint32_t all_bins_path;  /* GRIM_PATH_* (0 = automatic)   */
+  uint32_t reserved[3];
 } grim_build_opts;
 
 /* The coarse factor grim_build_ex chooses when opts->coarse_factor is 0. */
@@ -166,12 +180,13 @@ int grim_build_host_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q,
 int grim_index_info(const grim_index* idx, grim_index_desc* out);
 
 /*
- * Launch shape of the all-bins kernel for later calls with this index (the
+ * Launch shape of the all-bins filter for later calls with this index (the
  * tile sizes the paper ties to its parallel width p, §Parameter Evaluation
  * Results: how many bins' bits one fetch covers and how many reads reuse
  * it).  The bin tile is fixed by shared memory (1024 bins up to q = 5, 256
  * at q = 6; the coarse factor of grim_build_opts sets how many bins a
- * super-bin holds); this sets the rest:
+ * super-bin holds); a grim_shape sets the rest (zero fields: the default;
+ * shape NULL: every default):
  *   cta_threads    threads of the one persistent CTA per SM: 512, 640 or 768
  *                  (more warps, fewer registers each); 0 = 640
  *   read_range_kb  read tile: reads are swept in ranges of about this many
@@ -188,12 +203,21 @@ int grim_index_info(const grim_index* idx, grim_index_desc* out);
  *                  batch spans the same number of 16-token blocks (so no
  *                  group idles for long), GROUP otherwise; graph plans, whose
  *                  batches are not known when they are captured, use GROUP
+ *   all_bins_path  GRIM_PATH_TWO_LEVEL, GRIM_PATH_EXACT, or 0 (automatic; see
+ *                  GRIM_PATH_*)
  * Results do not depend on the shape.  Graph plans take the shape when they
  * are created.  Not to be called while a filter call with this index runs.
- * Errors: GRIM_E_ARG (NULL index, a value outside the ranges above).
+ * Errors: GRIM_E_ARG (NULL index, a value outside the ranges above),
+ * GRIM_E_NO_LAYOUT (a path whose tables the index lacks).
  */
-int grim_index_set_shape(grim_index* idx, uint32_t cta_threads, uint32_t read_range_kb,
-                         uint32_t read_switch);
+typedef struct {
+  uint32_t cta_threads;
+  uint32_t read_range_kb;
+  uint32_t read_switch;
+  uint32_t all_bins_path;
+  uint32_t reserved[4];
+} grim_shape;
+int grim_index_set_shape(grim_index* idx, const grim_shape* shape);
 
 /*
  * Index persistence (§GRIM-Filter: the bit vectors are generated once per

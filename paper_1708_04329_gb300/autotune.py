@@ -6,8 +6,8 @@ reads with CUDA events:
 * all-bins mode (``tune_all_bins``), by coordinate descent:
   - the bin tile: the coarse factor f (bins per super-bin of the coarse
     table) among the power-of-two neighbours of the presence-model default,
-    or one exact pass over every bin (f = 0); each needs its own index build
-    (~0.1 s at 3.1 Gbp);
+    each with its own index build (~0.1 s at 3.1 Gbp) and the two-level path,
+    or one exact pass over every bin;
   - the CTA size of the persistent kernel (512, 640 or 768 threads: warps
     per SM against registers per thread);
   - the read tile: KiB of token rows per read range (a range stays in L2
@@ -96,12 +96,12 @@ def tune_all_bins(ref, B: int, q: int, max_read_len: int, sample: dict,
 
     ref: uint8 CUDA tensor of the reference; sample: the grim_filter keyword
     arguments (reads, offsets, lens, e) of representative reads, enough to
-    fill the GPU (a hundred thousand or more).  Read ranges are only compared
+    fill the GPU (tens of thousands or more).  Read ranges are only compared
     when the sample's token rows span more than one of them.  Returns
-    {"factor": f (0 = one exact pass), "cta_threads": t, "read_range_kb": r,
-    "read_switch": w, "ms": {trial: ms}}; build the index with
-    grim_build_ex(..., coarse_factor=f, cta_threads=t, read_range_kb=r,
-    read_switch=w) and, for f = 0, without the coarse layout.
+    {"factor": f, "all_bins_path": GRIM_PATH_TWO_LEVEL or GRIM_PATH_EXACT,
+    "cta_threads": t, "read_range_kb": r, "read_switch": w, "ms": {trial: ms}};
+    build the index with grim_build_ex(..., coarse_factor=f, cta_threads=t,
+    read_range_kb=r, read_switch=w, all_bins_path=p).
     """
     n = int(sample["lens"].numel())
     key = (f"allbins|{int(ref.numel())}|{B}|{q}|{max_read_len}|{n}|"
@@ -109,16 +109,17 @@ def tune_all_bins(ref, B: int, q: int, max_read_len: int, sample: dict,
     table = _load(cache)
     if key in table:
         return table[key]
+    f0 = grim.grim_default_coarse_factor(B, q, max_read_len)
     if factors is None:
-        f0 = grim.grim_default_coarse_factor(B, q, max_read_len)
         factors = sorted({max(2, f0 // 2), f0, min(64, f0 * 2)})
-        factors = [f0] + [f for f in factors if f != f0] + [0]
+    factors = [f0] + [f for f in factors if f != f0]
+    two, exact = grim.GRIM_PATH_TWO_LEVEL, grim.GRIM_PATH_EXACT
     ws = grim.Workspace()
     ms = {}
 
-    def build(f):
-        layouts = grim.GRIM_LAYOUT_TOKEN_MAJOR if f == 0 else grim.GRIM_LAYOUT_ALL
-        return grim.grim_build_ex(ref, B, q, max_read_len, layouts, f)
+    def build(f, path):
+        return grim.grim_build_ex(ref, B, q, max_read_len, grim.GRIM_LAYOUT_ALL, f,
+                                  all_bins_path=path)
 
     def run(index):
         return _time(lambda: grim.grim_filter(index, **sample, workspace=ws), repeats)
@@ -132,30 +133,37 @@ def tune_all_bins(ref, B: int, q: int, max_read_len: int, sample: dict,
                 best = o
         return best
 
-    # 1. bin tile, at the default launch shape (the first factor is the default)
+    # 1. bin tile: the two-level path at each coarse factor (the first is the
+    #    default), and one exact pass, at the default launch shape
     for f in factors:
-        index = build(f)
+        index = build(f, two)
         try:
             ms[f"f={f}"] = run(index)
+            if f == f0:
+                grim.grim_index_set_shape(index, all_bins_path=exact)
+                ms["exact"] = run(index)
         finally:
             index.close()
     best_f = pick(factors[0], factors, "f")
-    index = build(best_f)
+    path = exact if ms["exact"] < ms[f"f={best_f}"] * (1.0 - min_gain) else two
+    if path == exact:
+        best_f = f0
+    index = build(best_f, path)
     try:
         d = index.desc
         best_t, best_r, best_w = d.cta_threads, d.read_range_kb, d.read_switch
-        ms[f"threads={best_t}"] = ms[f"f={best_f}"]
+        ms[f"threads={best_t}"] = ms["exact" if path == exact else f"f={best_f}"]
         # 2. CTA size
         for t in threads:
             if t != best_t:
-                grim.grim_index_set_shape(index, t, best_r, best_w)
+                grim.grim_index_set_shape(index, t, best_r, best_w, path)
                 ms[f"threads={t}"] = run(index)
         best_t = pick(best_t, threads, "threads")
         ms[f"switch={best_w}"] = ms[f"threads={best_t}"]
         # 3. read switch
         for w in switches:
             if w != best_w:
-                grim.grim_index_set_shape(index, best_t, best_r, w)
+                grim.grim_index_set_shape(index, best_t, best_r, w, path)
                 ms[f"switch={w}"] = run(index)
         best_w = pick(best_w, switches, "switch")
         ms[f"range_kb={best_r}"] = ms[f"switch={best_w}"]
@@ -163,14 +171,14 @@ def tune_all_bins(ref, B: int, q: int, max_read_len: int, sample: dict,
         tb = _token_bytes(n, q, max_read_len)
         tried = [r for r in ranges_kb if (r << 10) < tb and r != best_r]
         for r in tried:
-            grim.grim_index_set_shape(index, best_t, r, best_w)
+            grim.grim_index_set_shape(index, best_t, r, best_w, path)
             ms[f"range_kb={r}"] = run(index)
         best_r = pick(best_r, tried, "range_kb")
     finally:
         index.close()
-    out = {"factor": int(best_f), "cta_threads": int(best_t), "read_range_kb": int(best_r),
-           "read_switch": int(best_w), "ms": {k: round(v, 3) for k, v in ms.items()},
-           "sample_reads": n}
+    out = {"factor": int(best_f), "all_bins_path": int(path), "cta_threads": int(best_t),
+           "read_range_kb": int(best_r), "read_switch": int(best_w),
+           "ms": {k: round(v, 3) for k, v in ms.items()}, "sample_reads": n}
     table[key] = out
     _store(cache, table)
     return out

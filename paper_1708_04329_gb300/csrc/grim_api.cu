@@ -32,14 +32,29 @@ int cuda_fail(cudaError_t e) {
 // tokens if the sequence were uniform random (1 - exp(-q-grams / 4^q)); a
 // denser coarse table lets too many super-bins pass.  q = 5, B = 200,
 // ext = 99 gives 2; q = 6, B = 100, ext = 149 gives 16.
-uint32_t default_coarse_factor(uint32_t B, uint32_t q, uint32_t ext) {
+// Fraction of the 4^q tokens a super-bin window of f bins (f*B + ext bases)
+// would hold in a uniform random sequence.
+double coarse_density(uint32_t B, uint32_t q, uint32_t ext, uint32_t f) {
   const double tokens = (double)(1u << (2 * q));
+  const double grams = (double)f * B + ext - q + 1;
+  return 1.0 - exp(-grams / tokens);
+}
+constexpr double kCoarseDensityMax = 0.40;
+
+uint32_t default_coarse_factor(uint32_t B, uint32_t q, uint32_t ext) {
   uint32_t best = 2;
-  for (uint32_t f = 2; f <= 64; f *= 2) {
-    const double grams = (double)f * B + ext - q + 1;
-    if (1.0 - exp(-grams / tokens) <= 0.40) best = f;
-  }
+  for (uint32_t f = 2; f <= 64; f *= 2)
+    if (coarse_density(B, q, ext, f) <= kCoarseDensityMax) best = f;
   return best;
+}
+
+// A launch shape the index can run: an explicit path needs its tables.
+int shape_fits(const grim_index* idx, const ExhShape& s) {
+  if (!exhaustive_shape_ok(s) || s.path > GRIM_PATH_EXACT) return GRIM_E_ARG;
+  if (s.path == GRIM_PATH_EXACT && !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR))
+    return GRIM_E_NO_LAYOUT;
+  if (s.path == GRIM_PATH_TWO_LEVEL && !two_level_capable(idx)) return GRIM_E_NO_LAYOUT;
+  return GRIM_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -149,6 +164,7 @@ int index_alloc(uint64_t len, uint32_t B, uint32_t q, uint32_t max_read_len, uin
     e = table(&ix->presence, (uint64_t)v.r4 * sizeof(uint32_t));
     if (e != cudaSuccess) return fail(e);
   }
+  ix->coarse_pays = coarse_density(B, q, v.ext, f) <= kCoarseDensityMax;
   v.tm = ix->tm;
   v.bm = ix->bm;
   v.bm_rows = bm_bins;
@@ -298,8 +314,10 @@ int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_
   if (!out) return GRIM_E_ARG;
   *out = nullptr;
   if (!ref || B == 0 || max_read_len < q) return GRIM_E_ARG;
-  if (opts && !exhaustive_shape_ok({opts->cta_threads, opts->read_range_kb, opts->read_switch}))
-    return GRIM_E_ARG;
+  const ExhShape shape = opts ? ExhShape{opts->cta_threads, opts->read_range_kb, opts->read_switch,
+                                          opts->all_bins_path}
+                              : ExhShape{0, 0, 0, 0};
+  if (!exhaustive_shape_ok(shape) || shape.path > GRIM_PATH_EXACT) return GRIM_E_ARG;
   const uint32_t f = (opts && opts->coarse_factor) ? opts->coarse_factor
                      : (q >= 2 && q <= 6)              ? default_coarse_factor(B, q, max_read_len - 1)
                                                        : 2u;  // q is refused by index_alloc
@@ -307,7 +325,14 @@ int grim_build_ex(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint32_
   grim_index* ix = nullptr;
   const int rc = index_alloc(len, B, q, max_read_len, layouts, f, &ix);
   if (rc != GRIM_OK) return rc;
-  if (opts) ix->shape = ExhShape{opts->cta_threads, opts->read_range_kb, opts->read_switch};
+  {
+    const int fit = shape_fits(ix, shape);
+    if (fit != GRIM_OK) {
+      grim_free(ix);
+      return fit;
+    }
+    ix->shape = shape;
+  }
   const IndexView& v = ix->v;
   const IndexView& cv = ix->cv;
   const uint64_t bm_bins = cv.num_bins * f;
@@ -425,13 +450,19 @@ int grim_index_info(const grim_index* idx, grim_index_desc* out) {
   out->cta_threads = idx->shape.threads ? idx->shape.threads : 640u;
   out->read_range_kb = idx->shape.range_kb ? idx->shape.range_kb : (48u << 10);
   out->read_switch = idx->shape.read_switch;
+  out->all_bins_path = idx->shape.path;
+  bool forced = false;
+  out->two_level = all_bins_path(idx, &forced) == kPathCoarse ? 1u : 0u;
   return GRIM_OK;
 }
 
-int grim_index_set_shape(grim_index* idx, uint32_t cta_threads, uint32_t read_range_kb,
-                         uint32_t read_switch) {
-  const ExhShape s{cta_threads, read_range_kb, read_switch};
-  if (!idx || !exhaustive_shape_ok(s)) return GRIM_E_ARG;
+int grim_index_set_shape(grim_index* idx, const grim_shape* shape) {
+  if (!idx) return GRIM_E_ARG;
+  const ExhShape s = shape ? ExhShape{shape->cta_threads, shape->read_range_kb,
+                                      shape->read_switch, shape->all_bins_path}
+                           : ExhShape{0, 0, 0, 0};
+  const int rc = shape_fits(idx, s);
+  if (rc != GRIM_OK) return rc;
   idx->shape = s;
   return GRIM_OK;
 }
@@ -524,7 +555,8 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
     // needs enough of its tokens present for super-bins to fail early;
     // otherwise (some read passes almost anywhere) one exact pass
     const uint32_t min_slack = 255u - h.max_tight;
-    bool two = capable && (min_slack >= 24 || !(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR));
+    bool forced = false;
+    bool two = all_bins_path(idx, &forced) == kPathCoarse && (forced || min_slack >= 24);
     // automatic read switch: a warp's lane groups take their next reads
     // together when every read has as many 16-token blocks (no group waits
     // long for the others), each on its own otherwise

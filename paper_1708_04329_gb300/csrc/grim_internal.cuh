@@ -147,17 +147,21 @@ uint32_t exhaustive_tile_bins(uint32_t r4);
 // in L2 while the CTAs sweep their tiles), and how the lane groups of a warp
 // take their next reads (GRIM_SWITCH_GROUP: each group as its read ends;
 // GRIM_SWITCH_WARP: all groups of the warp together; 0 at launch = GROUP).
+// `path` (GRIM_PATH_*) is the index's all-bins path: coarse-then-exact or
+// one exact pass (0 = chosen per index, see all_bins_path).
 struct ExhShape {
   uint32_t threads;
   uint32_t range_kb;
   uint32_t read_switch;
+  uint32_t path;
 };
+// the launch shape's threads, range and read switch are ones the kernel builds
 bool exhaustive_shape_ok(const ExhShape& s);
 // max_d: the batch's largest miss budget (sizes the bit-sliced counters)
 void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec, uint32_t bin_bits,
                        uint32_t max_d, Ctl* ctl, cudaStream_t st,
                        const char* prof_name = "exhaustive", Live live = {false, 0},
-                       ExhShape shape = {0, 0, 0});
+                       ExhShape shape = {0, 0, 0, 0});
 // unroll: candidate gathers in flight per lane group (1, 2, 4 or 8; 0 =
 // default).  check_ids: the lists are the caller's; an id outside
 // [0, num_bins) sets kStatusBadCand (and is not gathered).  Internal lists
@@ -280,6 +284,10 @@ struct grim_index {
   uint32_t factor;
   uint32_t layouts;
   grim::ExhShape shape;  // launch shape of the all-bins kernel (grim_index_set_shape)
+  // the coarse table is sparse enough for the coarse pass to pay: its
+  // super-bin window would hold at most 40% of the 4^q tokens in a uniform
+  // random sequence (the rule that picks the default coarse factor)
+  bool coarse_pays;
   uint32_t* tm;
   uint32_t* bm;
   uint32_t* ctm;
@@ -302,5 +310,20 @@ int record_cuda_error(cudaError_t e);
 // coarse table and the bin-major table
 inline bool two_level_capable(const grim_index* idx) {
   return (idx->layouts & GRIM_LAYOUT_COARSE) && (idx->layouts & GRIM_LAYOUT_BIN_MAJOR);
+}
+
+// The all-bins path of an index's calls before the per-batch rules (a
+// batch with less than 24 tokens of slack takes the exact pass, and so do
+// coarse survivors that overflow their room): kPathCoarse or kPathExact.
+// *forced: the index leaves no choice, or the caller fixed the path
+// (GRIM_PATH_*), so the slack rule does not apply.
+inline uint32_t all_bins_path(const grim_index* idx, bool* forced) {
+  *forced = true;
+  if (!two_level_capable(idx)) return kPathExact;
+  if (!(idx->layouts & GRIM_LAYOUT_TOKEN_MAJOR)) return kPathCoarse;
+  if (idx->shape.path == GRIM_PATH_EXACT) return kPathExact;
+  if (idx->shape.path == GRIM_PATH_TWO_LEVEL) return kPathCoarse;
+  *forced = false;
+  return idx->coarse_pays ? kPathCoarse : kPathExact;
 }
 }  // namespace grim

@@ -68,10 +68,10 @@ enum : uint32_t { kCtlDecide = 1, kCtlAfterCoarse = 2, kCtlFinal = 3 };
 
 // One thread: the per-batch decisions that grim_filter takes on the host.
 __global__ void k_plan_control(Ctl* c, uint32_t op, uint32_t capable, uint32_t has_exact,
-                               unsigned long long rcap) {
+                               unsigned long long rcap, uint32_t forced) {
   if (op == kCtlDecide) {
     const uint32_t min_slack = 255u - c->max_tight;
-    c->path = (capable && (min_slack >= 24 || !has_exact)) ? kPathCoarse : kPathExact;
+    c->path = (capable && (forced || min_slack >= 24 || !has_exact)) ? kPathCoarse : kPathExact;
   } else if (op == kCtlAfterCoarse) {
     if (c->path == kPathCoarse) {
       c->n_surv = c->n_rec;
@@ -157,12 +157,14 @@ int capture(grim_plan* p) {
     launch_check_candidates(B.cand_off, d.max_reads, d.max_cand, p->ctl, st, live);
     launch_candidates(v, rv, B.cand, B.cand_off, ra, p->ctl, st, "candidates", live,
                       d.cand_unroll, true);
-    k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlFinal, 0, 0, 0);
+    k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlFinal, 0, 0, 0, 0);
     sort_and_emit(ra, rb, d.cap, bit_length(d.max_cand ? d.max_cand - 1 : 0), ws + L.hist, true,
                   bin_bits, B.cand, B.cand_off, d.max_reads, B.out_read,
                   B.out_bin, B.out_count, st, &p->ctl->n_final, &p->ctl->live_reads);
   } else {
-    k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlDecide, p->f != 0, has_exact, rcap);
+    bool forced = false;
+    all_bins_path(idx, &forced);
+    k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlDecide, p->f != 0, has_exact, rcap, forced);
     int32_t* icand = reinterpret_cast<int32_t*>(ws + L.cand);
     uint64_t* ioff = reinterpret_cast<uint64_t*>(ws + L.cand_off);
     const uint32_t cbits =
@@ -171,7 +173,7 @@ int capture(grim_plan* p) {
       const Live coarse{true, kPathCoarse};
       launch_exhaustive(idx->cv, rv, ra, cbits, max_d, p->ctl, st, "exhaustive_coarse", coarse,
                         idx->shape);
-      k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlAfterCoarse, 1, has_exact, rcap);
+      k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlAfterCoarse, 1, has_exact, rcap, 0);
       const RecordsView surv = sort_records(ra, rb, rcap, read_bits + cbits, ws + L.hist, st,
                                             &p->ctl->n_surv, p->ctl, kPathCoarse);
       expand_survivors(surv.keys, rcap, cbits, p->f, d.max_reads, icand, ioff, st, p->ctl,
@@ -183,7 +185,7 @@ int capture(grim_plan* p) {
       const Live exact{true, kPathExact};
       launch_exhaustive(v, rv, ra, bin_bits, max_d, p->ctl, st, "exhaustive", exact, idx->shape);
     }
-    k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlFinal, 0, 0, 0);
+    k_plan_control<<<1, 1, 0, st>>>(p->ctl, kCtlFinal, 0, 0, 0, 0);
     if (p->f) {
       sort_and_emit(ra, rb, d.cap, bit_length(rcap * p->f - 1), ws + L.hist, true, bin_bits, icand,
                     ioff, d.max_reads, B.out_read, B.out_bin, B.out_count, st,
@@ -239,7 +241,8 @@ int grim_plan_create(const grim_index* idx, const grim_plan_desc* desc, grim_pla
   p->d = *desc;
   p->cand_mode = cand_mode;
   p->hio = hio;
-  p->f = (!cand_mode && two_level_capable(idx)) ? idx->factor : 0;
+  bool forced = false;
+  p->f = (!cand_mode && all_bins_path(idx, &forced) == kPathCoarse) ? idx->factor : 0;
   p->L = layout(idx->v, desc->max_reads, desc->cap, p->f, token_copies(idx->v, cand_mode));
   const uint64_t n = desc->max_reads;
   const uint64_t mc = cand_mode ? desc->max_cand : 0;

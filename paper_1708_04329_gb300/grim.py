@@ -35,6 +35,8 @@ GRIM_E_CANCELLED = -16
 GRIM_LOAD_VERIFY = 1
 GRIM_SWITCH_GROUP = 1
 GRIM_SWITCH_WARP = 2
+GRIM_PATH_TWO_LEVEL = 1
+GRIM_PATH_EXACT = 2
 GRIM_PLAN_CANDIDATES = 1
 GRIM_PLAN_HOST_IO = 2
 
@@ -78,7 +80,8 @@ class _Desc(C.Structure):
                 ("num_coarse", C.c_uint64), ("num_coarse_pad", C.c_uint64),
                 ("coarse_token_major_bytes", C.c_uint64), ("coarse_factor", C.c_uint32),
                 ("cta_threads", C.c_uint32), ("read_range_kb", C.c_uint32),
-                ("read_switch", C.c_uint32)]
+                ("read_switch", C.c_uint32), ("all_bins_path", C.c_uint32),
+                ("two_level", C.c_uint32)]
 
 
 class _Stats(C.Structure):
@@ -90,6 +93,12 @@ class _Stats(C.Structure):
 class _BuildOpts(C.Structure):
     _fields_ = [("coarse_factor", C.c_uint32), ("cta_threads", C.c_uint32),
                 ("read_range_kb", C.c_uint32), ("read_switch", C.c_uint32),
+                ("all_bins_path", C.c_uint32), ("reserved", C.c_uint32 * 3)]
+
+
+class _Shape(C.Structure):
+    _fields_ = [("cta_threads", C.c_uint32), ("read_range_kb", C.c_uint32),
+                ("read_switch", C.c_uint32), ("all_bins_path", C.c_uint32),
                 ("reserved", C.c_uint32 * 4)]
 
 
@@ -159,7 +168,7 @@ def _lib() -> C.CDLL:
         lib.grim_index_info.restype = i32
         lib.grim_index_info.argtypes = [vp, C.POINTER(_Desc)]
         lib.grim_index_set_shape.restype = i32
-        lib.grim_index_set_shape.argtypes = [vp, u32, u32, u32]
+        lib.grim_index_set_shape.argtypes = [vp, C.POINTER(_Shape)]
         lib.grim_free.restype = None
         lib.grim_free.argtypes = [vp]
         lib.grim_strerror.restype = C.c_char_p
@@ -336,6 +345,8 @@ class IndexDesc:
     cta_threads: int = 0
     read_range_kb: int = 0
     read_switch: int = 0
+    all_bins_path: int = 0
+    two_level: int = 0
 
 
 class GrimIndex:
@@ -423,11 +434,12 @@ def grim_build_host(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_
 
 def grim_build_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
                   coarse_factor: int = 0, stream=None, cta_threads: int = 0,
-                  read_range_kb: int = 0, read_switch: int = 0) -> GrimIndex:
+                  read_range_kb: int = 0, read_switch: int = 0,
+                  all_bins_path: int = 0) -> GrimIndex:
     """grim_build_ex: grim_build with build options (``coarse_factor``: bins per
     super-bin of the coarse table; ``cta_threads``, ``read_range_kb``: the
     all-bins kernel's launch shape; 0 = the library default)."""
-    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb, read_switch)
+    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb, read_switch, all_bins_path)
     h = C.c_void_p()
     rc = _lib().grim_build_ex(_dptr(ref, "ref", 1), ref.numel(), B, q, max_read_len, layouts,
                               C.byref(opts), _stream_ptr(stream), C.byref(h))
@@ -438,11 +450,12 @@ def grim_build_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LA
 
 def grim_build_host_ex(ref, B: int, q: int, max_read_len: int, layouts: int = GRIM_LAYOUT_ALL,
                        coarse_factor: int = 0, stream=None, cta_threads: int = 0,
-                       read_range_kb: int = 0, read_switch: int = 0) -> GrimIndex:
+                       read_range_kb: int = 0, read_switch: int = 0,
+                       all_bins_path: int = 0) -> GrimIndex:
     """grim_build_host_ex: grim_build_host with build options."""
     p, keep = _hptr(ref, "ref", np.uint8)
     n = keep.numel() if hasattr(keep, "numel") else keep.size
-    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb, read_switch)
+    opts = _BuildOpts(coarse_factor, cta_threads, read_range_kb, read_switch, all_bins_path)
     h = C.c_void_p()
     rc = _lib().grim_build_host_ex(p, n, B, q, max_read_len, layouts, C.byref(opts),
                                    _stream_ptr(stream), C.byref(h))
@@ -526,16 +539,18 @@ def grim_index_info(index: GrimIndex) -> IndexDesc:
                      d.layouts, d.words_per_bin, d.token_major or 0, d.bin_major or 0,
                      d.token_major_bytes, d.bin_major_bytes, d.coarse_token_major or 0,
                      d.num_coarse, d.num_coarse_pad, d.coarse_token_major_bytes, d.coarse_factor,
-                     d.cta_threads, d.read_range_kb, d.read_switch)
+                     d.cta_threads, d.read_range_kb, d.read_switch, d.all_bins_path,
+                     d.two_level)
 
 
 def grim_index_set_shape(index: GrimIndex, cta_threads: int = 0, read_range_kb: int = 0,
-                         read_switch: int = 0) -> None:
-    """Launch shape of the all-bins kernel for later calls with this index:
+                         read_switch: int = 0, all_bins_path: int = 0) -> None:
+    """Launch shape of the all-bins filter for later calls with this index:
     CTA threads (512, 640 or 768), the read tile in KiB of token rows per
-    read range, and GRIM_SWITCH_GROUP / GRIM_SWITCH_WARP; 0 restores a
-    default."""
-    rc = _lib().grim_index_set_shape(index.handle, cta_threads, read_range_kb, read_switch)
+    read range, GRIM_SWITCH_GROUP / GRIM_SWITCH_WARP, and GRIM_PATH_TWO_LEVEL
+    / GRIM_PATH_EXACT; 0 restores a default (automatic)."""
+    shape = _Shape(cta_threads, read_range_kb, read_switch, all_bins_path)
+    rc = _lib().grim_index_set_shape(index.handle, C.byref(shape))
     if rc != GRIM_OK:
         raise GrimError(rc, "grim_index_set_shape")
 

@@ -101,8 +101,8 @@ def test_gather_probe_library_exports():
 def test_launch_shape_options_checked_before_any_device_work():
     """grim_build_ex refuses an all-bins launch shape it does not build (CTA
     sizes other than 512/640/768, read ranges outside 1 MiB..4 GiB, an
-    unknown read-switch mode) before it touches the reference pointer, and
-    grim_index_set_shape refuses a NULL index."""
+    unknown read-switch mode or all-bins path) before it touches the
+    reference pointer, and grim_index_set_shape refuses a NULL index."""
     import ctypes
 
     from paper_1708_04329_gb300 import grim
@@ -115,7 +115,7 @@ def test_launch_shape_options_checked_before_any_device_work():
         rc = lib.grim_build_ex(fake_ref, 1000, 200, 5, 100, 7, ctypes.byref(opts), None,
                                ctypes.byref(h))
         assert rc == grim.GRIM_E_ARG, (threads, range_kb)
-    assert lib.grim_index_set_shape(None, 640, 0, 0) == grim.GRIM_E_ARG
-    opts = grim._BuildOpts(0, 0, 0, 3)  # no such read-switch mode
-    assert lib.grim_build_ex(fake_ref, 1000, 200, 5, 100, 7, ctypes.byref(opts), None,
-                             ctypes.byref(h)) == grim.GRIM_E_ARG
+    assert lib.grim_index_set_shape(None, None) == grim.GRIM_E_ARG
+    for bad in (grim._BuildOpts(0, 0, 0, 3), grim._BuildOpts(0, 0, 0, 0, 3)):  # no such modes
+        assert lib.grim_build_ex(fake_ref, 1000, 200, 5, 100, 7, ctypes.byref(bad), None,
+                                 ctypes.byref(h)) == grim.GRIM_E_ARG
