@@ -1062,11 +1062,12 @@ def _plain_trace(idx, rs, trace, paced: bool, time_limit_s: float) -> dict:
             "completed_trace": len(lat) == len(trace["t"])}
 
 
-def serving_leg(g, trace_s: float = 10.0, load: float = 0.85) -> dict:
+def serving_leg(g, trace_s: float = 10.0, loads=(0.6, 0.85)) -> dict:
     """A short serving measurement for the headline line: the same genome's
     table (built for reads up to 250 bp) resident, the serving workload's
-    requests, capacity with the queue kept full, then a Poisson trace at
-    `load` of that capacity; latency percentiles of that trace."""
+    requests, capacity with the queue kept full, then a Poisson trace at each
+    of `loads` of that capacity; latency percentiles of those traces (the
+    last load is the line's headline serving point)."""
     import torch
 
     from paper_1708_04329_gb300 import grim, synth
@@ -1077,7 +1078,9 @@ def serving_leg(g, trace_s: float = 10.0, load: float = 0.85) -> dict:
     idx = grim.grim_build(ref, w["B"], w["q"], w["max_read_len"], grim.GRIM_LAYOUT_ALL)
     del ref
     torch.cuda.synchronize()
+    path = "two-level" if idx.desc.two_level else "one exact pass"
     slot_reads = 16384
+    points = []
     try:
         with grim.grim_server_create(idx, slots=3, max_reads=slot_reads,
                                      max_bases=slot_reads * 250, max_e=int(rs.e.max()),
@@ -1087,20 +1090,29 @@ def serving_leg(g, trace_s: float = 10.0, load: float = 0.85) -> dict:
             cap_run = _serve_trace(srv, rs, synth.request_trace(100.0, 1000.0, rs.n, seed=61),
                                    paced=False, time_limit_s=3.0)
             capacity = cap_run["requests"] / cap_run["elapsed_s"]
-            rate = load * capacity
-            main = _serve_trace(srv, rs, synth.request_trace(trace_s, rate, rs.n, seed=63),
-                                paced=True)
+            for i, load in enumerate(loads):
+                rate = load * capacity
+                r = _serve_trace(srv, rs, synth.request_trace(trace_s, rate, rs.n, seed=63 + i),
+                                 paced=True)
+                points.append({"load": load, "offered_batches_per_s": round(rate, 1),
+                               "value": round(r["reads_per_s"], 1),
+                               "latency_ms": {k: round(r[k + "_ms"], 2)
+                                              for k in ("p50", "p99", "p999")},
+                               "queue_wait_ms": r["queue_wait_ms"],
+                               "batch_run_ms": r["batch_run_ms"],
+                               "mean_requests_per_batch": round(r["mean_requests_per_batch"], 2),
+                               "requests": r["requests"]})
     finally:
         idx.close()
-    return {"value": round(main["reads_per_s"], 1), "unit": UNIT,
-            "offered_batches_per_s": round(rate, 1), "load": load,
-            "latency_ms": {k: round(main[k + "_ms"], 2) for k in ("p50", "p99", "p999")},
+    main = points[-1]
+    return {"value": main["value"], "unit": UNIT,
+            "offered_batches_per_s": main["offered_batches_per_s"], "load": main["load"],
+            "latency_ms": main["latency_ms"],
             "capacity_reads_per_s": round(cap_run["reads_per_s"], 1),
-            "mean_requests_per_batch": round(main["mean_requests_per_batch"], 2),
-            "queue_wait_ms": main["queue_wait_ms"], "batch_run_ms": main["batch_run_ms"],
-            "trace": (f"{trace_s:.0f} s Poisson trace, {main['requests']} requests, sizes "
-                      "log-uniform 1..8192, L in {100,150,250}, e <= 0.05 L; 3 slots; "
-                      "bench.py --workload serve runs the full 60 s measurement")}
+            "all_bins_path": path, "curve": points,
+            "trace": (f"{trace_s:.0f} s Poisson traces at {', '.join(str(x) for x in loads)} of "
+                      "capacity, sizes log-uniform 1..8192, L in {100,150,250}, e <= 0.05 L; "
+                      "3 slots; bench.py --workload serve runs the full sweep and a 60 s trace")}
 
 
 def run_serve(args, rank, world, local):
