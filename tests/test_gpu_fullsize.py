@@ -101,3 +101,30 @@ def test_properties_at_full_size(human):
     assert (pos < len(key)).all() and (key[pos] == true_key).all()
     exact = rs.n_edits[np.arange(rs.n)] == 0
     assert (c[pos[exact]] == 96).all()
+
+
+def test_exact_pass_equals_two_level_at_full_size(human):
+    """The one exact pass over every bin (the benchmark's exact leg) and the
+    coarse-then-exact path are independent routes through different tables
+    and kernels; on the full workload their pass lists must agree record for
+    record, and the exact pass must agree with the oracle on sampled reads."""
+    from paper_1708_04329_gb300 import grim
+
+    w, idx, got, oix = human
+    assert idx.desc.two_level == 1  # the headline takes the two-level path
+    grim.grim_index_set_shape(idx, all_bins_path=grim.GRIM_PATH_EXACT)
+    try:
+        exact = gpu_filter(idx, w["reads"], cap=8 * w["reads"].n)
+    finally:
+        grim.grim_index_set_shape(idx)
+    for a, b in zip(exact, got):
+        assert np.array_equal(a, b)
+    rs = w["reads"]
+    sample = np.linspace(3, rs.n - 4, 32).astype(np.int64)
+    want_r, want_b, want_c = oracle.filter(oix, rs.subset(sample))
+    r, b, c = exact
+    for j, ridx in enumerate(sample):
+        sel = r == ridx
+        ws = want_r == j
+        assert np.array_equal(b[sel], want_b[ws]), ridx
+        assert np.array_equal(c[sel], want_c[ws]), ridx
