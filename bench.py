@@ -99,6 +99,12 @@ def parse_args():
     p.add_argument("--serve-rate", type=float, default=0.0,
                    help="serve workload: offered batches/s of the measured trace (0: the "
                         "highest stable rate of the sweep)")
+    p.add_argument("--serve-slots", type=int, default=3, help="serve workload: slots")
+    p.add_argument("--serve-slot-reads", type=int, default=16384,
+                   help="serve workload: reads per slot (the largest merged batch)")
+    p.add_argument("--serve-quick", action="store_true",
+                   help="serve workload: capacity and the measured trace only (no sweep, no "
+                        "plain single-batch comparison)")
     p.add_argument("--serve-path", type=int, default=0,
                    help="serve workload: all-bins path (0 automatic, 1 two-level, 2 one exact pass)")
     p.add_argument("--serve-chunk", type=int, default=0,
@@ -1137,8 +1143,9 @@ def run_serve(args, rank, world, local):
                              all_bins_path=args.serve_path)
     del ref
     torch.cuda.synchronize()
-    slot_reads = 16384
-    srv = grim.grim_server_create(idx, slots=3, max_reads=slot_reads, max_bases=slot_reads * 250,
+    slot_reads = args.serve_slot_reads
+    srv = grim.grim_server_create(idx, slots=args.serve_slots, max_reads=slot_reads,
+                                  max_bases=slot_reads * 250,
                                   max_e=int(rs.e.max()), cap=32 * slot_reads,
                                   mem_budget=8 << 30, max_chunk_reads=args.serve_chunk)
     # warm-up, then capacity with the queue kept full (batches/s of the same size mix)
@@ -1148,7 +1155,7 @@ def run_serve(args, rank, world, local):
                            paced=False, time_limit_s=5.0)
     capacity = cap_run["requests"] / cap_run["elapsed_s"]
     sweep, best = [], None
-    for frac in (0.5, 0.7, 0.85, 0.95):
+    for frac in (() if args.serve_quick else (0.5, 0.7, 0.85, 0.95)):
         rate = frac * capacity
         r = _serve_trace(srv, rs, synth.request_trace(5.0, rate, rs.n, seed=62), paced=True)
         ok = r["drain_s"] < 1.0 and r["p99_ms"] < 1000.0
@@ -1169,9 +1176,11 @@ def run_serve(args, rank, world, local):
     st = srv.stats()
     srv.close()
     # the plain single-batch path on the same trace (bounded to 20 s), and its capacity
-    plain_cap = _plain_trace(idx, rs, synth.request_trace(100.0, 1000.0, rs.n, seed=61),
-                             paced=False, time_limit_s=5.0)
-    plain = _plain_trace(idx, rs, trace, paced=True, time_limit_s=20.0)
+    plain_cap = plain = None
+    if not args.serve_quick:
+        plain_cap = _plain_trace(idx, rs, synth.request_trace(100.0, 1000.0, rs.n, seed=61),
+                                 paced=False, time_limit_s=5.0)
+        plain = _plain_trace(idx, rs, trace, paced=True, time_limit_s=20.0)
     n_req = main["requests"]
     bytes_in = sum(int(rs.lens[s:s + n].sum()) + 14 * n for s, n in
                    zip(trace["start"], trace["size"]))
@@ -1199,7 +1208,7 @@ def run_serve(args, rank, world, local):
         "mean_requests_per_batch": round(main["mean_requests_per_batch"], 2),
         "capacity_reads_per_s": round(cap_run["reads_per_s"], 1),
         "sweep": sweep,
-        "plain_single_batch": {
+        "plain_single_batch": None if plain is None else {
             "capacity_reads_per_s": round(plain_cap["reads_per_s"], 1),
             "same_trace": {k: (round(v, 3) if isinstance(v, float) else v) for k, v in plain.items()}},
         "server_stats": st,

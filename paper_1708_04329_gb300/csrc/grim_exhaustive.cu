@@ -66,7 +66,7 @@ constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 // token rows of one read range: small enough to stay in L2 while every CTA
 // sweeps its tiles against the range
 constexpr uint64_t kDefaultRangeBytes = 48ull << 20;
-constexpr uint32_t kSlotBlocksNarrow = 1;  // slot blocks per read, 256-bin tiles
+constexpr uint32_t kSlotBlocksNarrow = 4;  // most slot blocks per read, 256-bin tiles
 
 #define LOP3(d, a, b, c, lut) \
   asm("lop3.b32 %0, %1, %2, %3, " #lut ";" : "=r"(d) : "r"(a), "r"(b), "r"(c))
@@ -530,22 +530,36 @@ void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec
   a.bin_bits = bin_bits;
   a.live = live;
   // a slot row holds a read's first blocks: all of them for the 1024-bin
-  // tiles; kSlotBlocksNarrow for the 256-bin tiles of q = 6, whose 128 KB
-  // tile leaves little room for the sixteen groups' slots of a warp -- the
-  // later blocks come from L2, and the warps that the smaller slots make
-  // room for hide that latency (measured at 768-thread CTAs: 1 block let
-  // 24 warps per SM fit, 7 blocks 11)
+  // tiles; for the 256-bin tiles of q = 6, whose 128 KB tile leaves little
+  // room for the sixteen groups' slots of a warp, as many (up to
+  // kSlotBlocksNarrow) as fit beside the tile at the CTA size -- the later
+  // blocks come from L2 (warps matter more than slot blocks: at 768-thread
+  // CTAs 1 block let 24 warps per SM fit, 7 blocks 11)
+  const uint32_t nt = shape.threads ? shape.threads : kDefaultThreads;
   const uint32_t blocks = rv.ts / kBlockTokens;
-  a.slot_blocks = ix.r4 <= 1024 ? blocks : min(blocks, kSlotBlocksNarrow);
-  a.row_stride = a.slot_blocks * kBlockTokens * 2u;
   // slots of consecutive groups start 32 bytes apart modulo 128, so the
   // groups of a warp mostly read their tokens from different banks
-  a.slot_bytes = (2u * a.row_stride + 127u) / 128u * 128u + 32u;
+  auto slot_bytes_of = [](uint32_t slot_blocks) {
+    return (2u * slot_blocks * kBlockTokens * 2u + 127u) / 128u * 128u + 32u;
+  };
+  if (ix.r4 <= 1024) {
+    a.slot_blocks = blocks;
+  } else {
+    const size_t tile_bytes = (size_t)(ix.r4 + 2) * 8u * 4u;
+    const uint32_t groups = nt / 2u;  // 2-lane groups
+    a.slot_blocks = 1;
+    for (uint32_t sb = min(blocks, kSlotBlocksNarrow); sb > 1; --sb)
+      if (tile_bytes + (size_t)groups * slot_bytes_of(sb) + 32 <= kSmemLimit) {
+        a.slot_blocks = sb;
+        break;
+      }
+  }
+  a.row_stride = a.slot_blocks * kBlockTokens * 2u;
+  a.slot_bytes = slot_bytes_of(a.slot_blocks);
   a.c_hi = 65536u;
   a.c_lo = 0u - 65536u;
   a.range_bytes = shape.range_kb ? (uint64_t)shape.range_kb << 10 : kDefaultRangeBytes;
   a.ctl = ctl;
-  const uint32_t nt = shape.threads ? shape.threads : kDefaultThreads;
   const bool ws = shape.read_switch == GRIM_SWITCH_WARP;
   if (ix.r4 <= 1024) launch_tw<32>(a, ix, max_d, (uint32_t)sms, nt, ws, st, prof_name);
   else launch_tw<8>(a, ix, max_d, (uint32_t)sms, nt, ws, st, prof_name);
