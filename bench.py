@@ -100,7 +100,7 @@ def parse_args():
                    help="serve workload: offered batches/s of the measured trace (0: the "
                         "highest stable rate of the sweep)")
     p.add_argument("--serve-slots", type=int, default=3, help="serve workload: slots")
-    p.add_argument("--serve-slot-reads", type=int, default=16384,
+    p.add_argument("--serve-slot-reads", type=int, default=8192,
                    help="serve workload: reads per slot (the largest merged batch)")
     p.add_argument("--serve-quick", action="store_true",
                    help="serve workload: capacity and the measured trace only (no sweep, no "
@@ -1085,7 +1085,7 @@ def serving_leg(g, trace_s: float = 10.0, loads=(0.6, 0.85)) -> dict:
     del ref
     torch.cuda.synchronize()
     path = "two-level" if idx.desc.two_level else "one exact pass"
-    slot_reads = 16384
+    slot_reads = 8192
     points = []
     try:
         with grim.grim_server_create(idx, slots=3, max_reads=slot_reads,
