@@ -51,12 +51,12 @@ UNIT = "reads/s"
 TRAFFIC = {
     # all-bins kernel, 1M reads of 100 bp (4 read ranges), linear in the
     # tiles swept: captures at 0.4 and 0.8 Gbp (977 and 1,954 coarse tiles:
-    # 1.298 and 2.191 GB per launch) give 0.405 GB + 0.914 MB per tile;
+    # 1.284 and 2.157 GB per launch) give 0.412 GB + 0.893 MB per tile;
     # 7,569 coarse tiles of the 3.1 Gbp table
-    ("9746ed514f533e03", "human:exhaustive_coarse"): 7_321_903_209,
+    ("5d28d0c8f7cfbc56", "human:exhaustive_coarse"): 7_170_444_984,
     # the same rule for the one exact pass over bins (1,954 and 3,907 tiles:
-    # 2.031 and 3.685 GB; 0.376 GB + 0.847 MB per tile); 15,137 tiles
-    ("9746ed514f533e03", "human:exhaustive_exact"): 13_193_542_521,
+    # 2.003 and 3.529 GB; 0.476 GB + 0.782 MB per tile); 15,137 tiles
+    ("5d28d0c8f7cfbc56", "human:exhaustive_exact"): 12_305_635_845,
     # candidate kernel, in proportion to the pairs gathered: the 3.1 Gbp
     # bin-major table (1.98 GB, as at full size) with 100k ragged reads,
     # 32,876,582 pairs, 4.314 GB (131.2 B per pair); 1,320,234,389 pairs
