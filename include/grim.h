@@ -580,7 +580,11 @@ typedef struct {
                                 every bin of the tile has failed                       */
   uint64_t survivors;        /* all-bins mode, coarse-then-exact: (read, super-bin)
                                 pairs that passed the coarse pass (0 otherwise)       */
-  uint64_t bit_tests_executed; /* all-bins mode: tokens_executed x (super-)bins per tile */
+  uint64_t bit_tests_executed; /* all-bins mode: tokens_executed x (super-)bins per tile,
+                                  except that a token of the one-word tail (1024-bin tiles,
+                                  warp read switch: the last blocks of a read once every
+                                  lane of the warp has at most one 32-bin word with a live
+                                  bin) tests 256 of the tile's bins                       */
 } grim_filter_stats;
 
 /* Counters of the calling thread's last successful grim_filter /

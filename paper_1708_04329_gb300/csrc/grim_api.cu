@@ -617,7 +617,10 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   g_last_stats.n_records = h.n_rec;
   g_last_stats.pairs = cand_mode ? n_cand : (uint64_t)n_reads * v.num_bins;
   g_last_stats.tokens_executed = h.blocks * kBlockTokens;
-  g_last_stats.bit_tests_executed = h.blocks * kBlockTokens * exhaustive_tile_bins(v.r4);
+  // blocks of the one-word tail test a quarter of the tile's bins
+  g_last_stats.bit_tests_executed =
+      (h.blocks - h.tail_blocks) * kBlockTokens * exhaustive_tile_bins(v.r4) +
+      h.tail_blocks * kBlockTokens * (exhaustive_tile_bins(v.r4) / 4);
   g_last_stats.survivors = survivors;
   return GRIM_OK;
 }

@@ -51,6 +51,15 @@
 //   together once every one of them has ended (one switch per warp per
 //   round of reads; a group that ends early applies padding tokens, which
 //   change nothing, until the others end).
+// * One-word tail (1024-bin tiles, warp switch): after four blocks of a
+//   round, if no lane of the warp has more than one word with a live bin,
+//   the warp keeps that word's counters and applies the round's remaining
+//   blocks to it alone (one 4-byte load and a quarter of the logic ops per
+//   token).  Past the first blocks the live bins of a tile usually sit in
+//   one or two words near the read's true position.  Register pressure
+//   decides whether this pays: the tail runs as its own inner loop so that
+//   the four-word loop stays as it was (a variant that chose the word count
+//   per block spilled and ran slower than no tail at all).
 #include "grim_internal.cuh"
 
 namespace grim {
@@ -67,6 +76,14 @@ constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 // sweeps its tiles against the range
 constexpr uint64_t kDefaultRangeBytes = 48ull << 20;
 constexpr uint32_t kSlotBlocksNarrow = 4;  // most slot blocks per read, 256-bin tiles
+// blocks a warp applies to all four words of its lanes before it checks for
+// the one-word tail (1024-bin tiles, warp-synchronous read switch)
+constexpr uint32_t kTailAfter = 4;
+
+template <int N>
+struct Words {
+  static constexpr int value = N;
+};
 
 #define LOP3(d, a, b, c, lut) \
   asm("lop3.b32 %0, %1, %2, %3, " #lut ";" : "=r"(d) : "r"(a), "r"(b), "r"(c))
@@ -104,6 +121,12 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
   return v;
 }
 
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
 template <int P>
 struct Counters {
   // per word: s1 s2 s4 s8 (weights 1..8), up[i] (weight 16 << i), dead
@@ -120,6 +143,22 @@ struct Counters {
       for (int i = 0; i < P - 4; ++i) up[i][w] = 0u - ((bias >> (4 + i)) & 1u);
       dead[w] = 0u;
     }
+  }
+
+  // One-word tail: keep only the counters of word k in slot 0 (dead unless
+  // `live`); slots 1..3 die.
+  __device__ __forceinline__ void keep_one(uint32_t k, bool live) {
+    auto sel = [k](const uint32_t(&x)[4]) {
+      return k == 0 ? x[0] : k == 1 ? x[1] : k == 2 ? x[2] : x[3];
+    };
+    s1[0] = sel(s1);
+    s2[0] = sel(s2);
+    s4[0] = sel(s4);
+    s8[0] = sel(s8);
+#pragma unroll
+    for (int i = 0; i < P - 4; ++i) up[i][0] = sel(up[i]);
+    dead[0] = live ? sel(dead) : ~0u;
+    dead[1] = dead[2] = dead[3] = ~0u;
   }
 
   // counter value of bin `bit` of word w
@@ -148,28 +187,40 @@ struct ExhArgs {
 };
 
 // Add the misses of one 16-token block.  tw holds 16 table row indices as
-// uint16 pairs; lane_base is the shared address of this lane's 16 bytes of
-// row 0.
-template <int P>
-__device__ __forceinline__ void add_block(Counters<P>& c, const uint32_t (&tw)[8],
-                                          uint32_t lane_base, const ExhArgs& a) {
+// uint16 pairs; base is the shared address of this lane's words in row 0.
+// NW = 4: all four words of the lane (one 16-byte load per token); NW = 1:
+// the one-word tail, counter slot 0 only, its word at `base`.
+template <int P, int NW>
+__device__ __forceinline__ void add_block(Counters<P>& c, const uint32_t (&tw)[8], uint32_t base,
+                                          const ExhArgs& a) {
+  static_assert(NW == 4 || NW == 1, "four words or one");
   uint32_t addr[16];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const uint32_t hi = imul_hi(tw[j], a.c_hi);     // token 2j+1
     const uint32_t lo = imad(hi, a.c_lo, tw[j]);    // token 2j
-    addr[2 * j] = imad(lo, a.c_row, lane_base);
-    addr[2 * j + 1] = imad(hi, a.c_row, lane_base);
+    addr[2 * j] = imad(lo, a.c_row, base);
+    addr[2 * j + 1] = imad(hi, a.c_row, base);
   }
-  uint32_t t2a[4], t2b[4], t4a[4], t4b[4], t8a[4], t8b[4], t16[4];
+  uint32_t t2a[NW], t2b[NW], t4a[NW], t4b[NW], t8a[NW], t8b[NW], t16[NW];
 #pragma unroll
   for (int quad = 0; quad < 4; ++quad) {
-    const uint4 x0 = lds128(addr[4 * quad]), x1 = lds128(addr[4 * quad + 1]);
-    const uint4 x2 = lds128(addr[4 * quad + 2]), x3 = lds128(addr[4 * quad + 3]);
-    const uint32_t a0[4] = {x0.x, x0.y, x0.z, x0.w}, a1[4] = {x1.x, x1.y, x1.z, x1.w};
-    const uint32_t a2[4] = {x2.x, x2.y, x2.z, x2.w}, a3[4] = {x3.x, x3.y, x3.z, x3.w};
+    uint32_t a0[NW], a1[NW], a2[NW], a3[NW];
+    if constexpr (NW == 4) {
+      const uint4 x0 = lds128(addr[4 * quad]), x1 = lds128(addr[4 * quad + 1]);
+      const uint4 x2 = lds128(addr[4 * quad + 2]), x3 = lds128(addr[4 * quad + 3]);
+      a0[0] = x0.x; a0[1] = x0.y; a0[2] = x0.z; a0[3] = x0.w;
+      a1[0] = x1.x; a1[1] = x1.y; a1[2] = x1.z; a1[3] = x1.w;
+      a2[0] = x2.x; a2[1] = x2.y; a2[2] = x2.z; a2[3] = x2.w;
+      a3[0] = x3.x; a3[1] = x3.y; a3[2] = x3.z; a3[3] = x3.w;
+    } else {
+      a0[0] = lds32(addr[4 * quad]);
+      a1[0] = lds32(addr[4 * quad + 1]);
+      a2[0] = lds32(addr[4 * quad + 2]);
+      a3[0] = lds32(addr[4 * quad + 3]);
+    }
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
+    for (int w = 0; w < NW; ++w) {
       uint32_t* t4 = (quad & 1) ? t4b : t4a;
       fa_miss(c.s1[w], a0[w], a1[w], c.s1[w], t2a[w]);
       fa_miss(c.s1[w], a2[w], a3[w], c.s1[w], t2b[w]);
@@ -278,19 +329,25 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
       asm volatile("cp.async.commit_group;");
     }
 
-    // which of this lane's 128 bins exist (only the last tile is ragged)
-    uint32_t vmask[4];
+    // which bins of this lane's words exist (only the last tile is ragged)
+    uint32_t vm[4];
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
       const uint64_t b0 = (uint64_t)tile * kTileBinsT + (li * 4u + w) * 32u;
       const uint64_t left = b0 < a.ix.num_bins ? a.ix.num_bins - b0 : 0;
-      vmask[w] = left >= 32 ? ~0u : ((1u << left) - 1u);
+      vm[w] = left >= 32 ? ~0u : ((1u << left) - 1u);
     }
+    auto vmask = [&](uint32_t w) -> uint32_t {
+      return w == 0 ? vm[0] : w == 1 ? vm[1] : w == 2 ? vm[2] : vm[3];
+    };
 
     // per-group state (identical in the group's 8 lanes); the group's slot
     // holds two token rows: `buf` is the current read's, buf^1 the next's
     uint32_t cur = kNone, nxt = kNone, nxt_meta = 0, buf = 1;
-    uint32_t nblk = 0, ntok = 0, bias = 0, executed = 0;
+    uint32_t nblk = 0, ntok = 0, bias = 0, executed = 0, tail_exec = 0;
+    // WS, 1024-bin tiles: blocks since the warp's last switch, and the word
+    // kept in the one-word tail
+    uint32_t bk = 0, kt = 0;
     bool fin = false;
     Counters<P> c;
     c.init(0);
@@ -361,9 +418,12 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
     bool active = __any_sync(0xFFFFFFFFu, !fin);
     bool waiting = false;  // WS: the group's read has ended; it waits for the warp's switch
 
-    while (active) {
-      // (2) one 16-token block for all groups: from the slot, or for the
-      //     blocks past the slot's rows (long reads at q = 6) from L2
+    // (2) one 16-token block for all groups, to NW words per lane: from the
+    //     slot, or for the blocks past the slot's rows (long reads at q = 6)
+    //     from L2; (3) then the end-of-read test.  True when the warp took
+    //     new reads.
+    auto run_block = [&](auto words) -> bool {
+      constexpr int NW = decltype(words)::value;
       {
         uint4 t0, t1;
         const uint32_t bi = nblk - left;  // this read's block index
@@ -378,13 +438,14 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
           t1 = __ldg(g + 1);
         }
         const uint32_t tw[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-        add_block<P>(c, tw, lane_base, a);
+        if constexpr (NW == 1) add_block<P, 1>(c, tw, lane_base + kt * 4u, a);
+        else add_block<P, 4>(c, tw, lane_base, a);
       }
       tp += step;
       --left;
 
-      // (3) a read ends when every bin of its tile is dead or its tokens are
-      //     used up; one ballot per block, the rest only when some group ends
+      // a read ends when every bin of its tile is dead or its tokens are
+      // used up; one ballot per block, the rest only when some group ends
       const uint32_t all_dead = c.dead[0] & c.dead[1] & c.dead[2] & c.dead[3];
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, all_dead == ~0u);
       const bool gdead = (bal & gmask) == gmask;
@@ -393,61 +454,102 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
         // freeze the group's counters (padding adds no misses) until every
         // group of the warp has ended its read
         executed += nblk - left;
+        if (NW == 1) tail_exec += nblk - left;
         waiting = true;
         tp = pad_tokens;
         step = 0;
       }
-      if (WS ? __all_sync(0xFFFFFFFFu, fin || waiting) : __any_sync(0xFFFFFFFFu, done)) {
-        if (WS) {
-          done = waiting;
-        } else if (done) {
-          executed += nblk - left;
+      if (!(WS ? __all_sync(0xFFFFFFFFu, fin || waiting) : __any_sync(0xFFFFFFFFu, done)))
+        return false;
+      if (WS) {
+        done = waiting;
+      } else if (done) {
+        executed += nblk - left;
+      }
+      const bool emit = done && !gdead;
+      if (__any_sync(0xFFFFFFFFu, emit)) {
+        // in the one-word tail slot 0 holds word kt and slots 1..3 are dead
+        uint32_t pm[4], cnt = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          pm[w] = emit ? (~c.dead[w] & vmask((NW == 1 && w == 0) ? kt : (uint32_t)w)) : 0u;
+          cnt += __popc(pm[w]);
         }
-        const bool emit = done && !gdead;
-        if (__any_sync(0xFFFFFFFFu, emit)) {
-          uint32_t pm[4], cnt = 0;
+        uint32_t incl = cnt;
 #pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            pm[w] = emit ? (~c.dead[w] & vmask[w]) : 0u;
-            cnt += __popc(pm[w]);
-          }
-          uint32_t incl = cnt;
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+          if (lane >= (uint32_t)d) incl += t;
+        }
+        const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        unsigned long long base = 0;
+        if (lane == 0 && tot) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)tot);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        unsigned long long pos = base + incl - cnt;
 #pragma unroll
-          for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-            if (lane >= (uint32_t)d) incl += t;
-          }
-          const uint32_t tot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-          unsigned long long base = 0;
-          if (lane == 0 && tot) base = atomicAdd(&a.ctl->n_rec, (unsigned long long)tot);
-          base = __shfl_sync(0xFFFFFFFFu, base, 0);
-          unsigned long long pos = base + incl - cnt;
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            uint32_t m = pm[w];
-            while (m) {
-              const uint32_t bit = __ffs(m) - 1;
-              m &= m - 1;
-              const uint32_t misses = c.value(w, bit) - bias;
-              const uint64_t bin = (uint64_t)tile * kTileBinsT + (li * 4u + w) * 32u + bit;
-              if (pos < a.rec.cap) {
-                a.rec.keys[pos] = ((unsigned long long)cur << a.bin_bits) | bin;
-                a.rec.counts[pos] = (uint8_t)(ntok - misses);
-              }
-              ++pos;
+        for (int w = 0; w < 4; ++w) {
+          uint32_t m = pm[w];
+          while (m) {
+            const uint32_t bit = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t misses = c.value(w, bit) - bias;
+            const uint32_t wi = (NW == 1 && w == 0) ? kt : (uint32_t)w;
+            const uint64_t bin = (uint64_t)tile * kTileBinsT + (li * 4u + wi) * 32u + bit;
+            if (pos < a.rec.cap) {
+              a.rec.keys[pos] = ((unsigned long long)cur << a.bin_bits) | bin;
+              a.rec.counts[pos] = (uint8_t)(ntok - misses);
             }
+            ++pos;
           }
         }
-        if (done) cur = kNone;
-        switch_reads(done);
-        waiting = false;
-        active = __any_sync(0xFFFFFFFFu, !fin);
+      }
+      if (done) cur = kNone;
+      switch_reads(done);
+      waiting = false;
+      active = __any_sync(0xFFFFFFFFu, !fin);
+      return true;
+    };
+
+    while (active) {
+      if (run_block(Words<4>{})) {
+        bk = 0;
+        continue;
+      }
+      if constexpr (WS && TW == 32) {
+        if (++bk != kTailAfter) continue;
+        // one-word tail: once every lane of the warp has at most one word
+        // with a live bin (typically only near a read's true position), the
+        // warp applies the rest of the round's blocks to that word alone: a
+        // quarter of the logic ops, one 4-byte load per token.  Exact: a
+        // word dropped here has no live bin (or only bins past the table's
+        // end), and dead bins never pass.
+        uint32_t lm = 0;
+        if (!fin) {
+#pragma unroll
+          for (int w = 0; w < 4; ++w)
+            if (~c.dead[w] & vmask(w)) lm |= 1u << w;
+        }
+        if (__all_sync(0xFFFFFFFFu, (lm & (lm - 1u)) == 0u)) {
+          kt = lm ? (uint32_t)__ffs(lm) - 1u : 0u;
+          c.keep_one(kt, lm != 0u);
+          // tail blocks of a read = its blocks when it ends - the first four
+          // (the subtraction wraps until the addition at its end)
+          if (!fin && !waiting) tail_exec -= kTailAfter;
+          while (!run_block(Words<1>{})) {
+          }
+          bk = 0;
+        }
       }
     }
     // one count per group (its lanes agree), one atomic per warp and item
     uint32_t ex = li == 0 ? executed : 0u;
     ex = __reduce_add_sync(0xFFFFFFFFu, ex);
     if (lane == 0 && ex) atomicAdd(&a.ctl->blocks, (unsigned long long)ex);
+    if constexpr (WS && TW == 32) {
+      uint32_t tx = li == 0 ? tail_exec : 0u;
+      tx = __reduce_add_sync(0xFFFFFFFFu, tx);
+      if (lane == 0 && tx) atomicAdd(&a.ctl->tail_blocks, (unsigned long long)tx);
+    }
   }
 }
 

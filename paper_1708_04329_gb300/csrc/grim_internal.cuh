@@ -37,7 +37,8 @@ struct Ctl {
   unsigned long long n_final;      // passing records of the batch
   uint32_t blk_max;                // most 16-token blocks of a read in the batch
   uint32_t blk_lo;                 // 32 - the fewest 16-token blocks of a read
-  uint32_t pad[44];
+  unsigned long long tail_blocks;  // of `blocks`: applied to one word per lane (256 bins)
+  uint32_t pad[42];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte slot");
 static_assert(offsetof(Ctl, live_reads) == 32, "live counts follow the per-pass counters");
