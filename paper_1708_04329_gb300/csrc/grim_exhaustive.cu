@@ -50,7 +50,9 @@
 //   ends (a switch for every read that ends), or all groups of a warp
 //   together once every one of them has ended (one switch per warp per
 //   round of reads; a group that ends early applies padding tokens, which
-//   change nothing, until the others end).
+//   change nothing, until the others end).  With sixteen groups (256-bin
+//   tiles) the warp switch comes once 14 of them wait; the other two keep
+//   their reads.
 // * One-word tail (1024-bin tiles, warp switch): after four blocks of a
 //   round, if no lane of the warp has more than one word with a live bin,
 //   the warp keeps that word's counters and applies the round's remaining
@@ -76,6 +78,8 @@ constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 // sweeps its tiles against the range
 constexpr uint64_t kDefaultRangeBytes = 48ull << 20;
 constexpr uint32_t kSlotBlocksNarrow = 4;  // most slot blocks per read, 256-bin tiles
+// WS, 256-bin tiles: groups of the sixteen that wait before the warp switches
+constexpr uint32_t kSwitchGroupsNarrow = 14;
 // blocks a warp applies to all four words of its lanes before it checks for
 // the one-word tail (1024-bin tiles, warp-synchronous read switch)
 constexpr uint32_t kTailAfter = 4;
@@ -183,6 +187,7 @@ struct ExhArgs {
   uint32_t slot_blocks; // 16-token blocks a slot row holds; later blocks come from L2
   uint32_t c_row, c_hi, c_lo;  // TW*4, 65536, -65536: multipliers of the address math
   uint64_t range_bytes;        // token-row bytes of one read range (the read tile)
+  uint32_t switch_lanes;       // WS, 256-bin tiles: waiting lanes that make the warp switch
   Ctl* ctl;
 };
 
@@ -459,8 +464,17 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
         tp = pad_tokens;
         step = 0;
       }
-      if (!(WS ? __all_sync(0xFFFFFFFFu, fin || waiting) : __any_sync(0xFFFFFFFFu, done)))
-        return false;
+      bool take_next;
+      if constexpr (!WS) {
+        take_next = __any_sync(0xFFFFFFFFu, done);
+      } else if constexpr (TW == 32) {
+        take_next = __all_sync(0xFFFFFFFFu, fin || waiting);
+      } else {
+        // sixteen groups: switch once enough of them wait, so that a few
+        // long reads do not hold the rest (the others keep their reads)
+        take_next = __popc(__ballot_sync(0xFFFFFFFFu, fin || waiting)) >= a.switch_lanes;
+      }
+      if (!take_next) return false;
       if (WS) {
         done = waiting;
       } else if (done) {
@@ -658,6 +672,7 @@ void launch_exhaustive(const IndexView& ix, const ReadsView& rv, RecordsView rec
   }
   a.row_stride = a.slot_blocks * kBlockTokens * 2u;
   a.slot_bytes = slot_bytes_of(a.slot_blocks);
+  a.switch_lanes = kSwitchGroupsNarrow * 2u;
   a.c_hi = 65536u;
   a.c_lo = 0u - 65536u;
   a.range_bytes = shape.range_kb ? (uint64_t)shape.range_kb << 10 : kDefaultRangeBytes;

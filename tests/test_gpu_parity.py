@@ -305,6 +305,27 @@ def test_q6_all_bins(layouts):
     assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
 
 
+@pytest.mark.parametrize("lengths", [(150,), (60, 150, 250)])
+def test_q6_read_switch_modes(lengths):
+    """q = 6, every read switch: with sixteen 2-lane groups per warp the warp
+    switch takes new reads once 14 groups wait, so the others keep reads that
+    started earlier (groups out of phase, token blocks past the slot read
+    from L2).  2,400 reads span several read ranges of a 1 MiB read tile;
+    uniform and mixed lengths; both all-bins paths; equal to the oracle."""
+    from paper_1708_04329_gb300 import grim, synth
+
+    g = synth.human_genome(600_000, seed=12)
+    rs = synth.reads(g, 2400, seed=13, lengths=lengths, probs=(1.0,) if len(lengths) == 1 else (0.3, 0.4, 0.3),
+                     e_frac=(5, 100), max_edits=None)
+    idx = build(g, 100, 6, 250)
+    want = oracle.filter(oracle.bin_vectors(g, 100, 6, 250), rs)
+    for path in (grim.GRIM_PATH_TWO_LEVEL, grim.GRIM_PATH_EXACT):
+        for switch in (grim.GRIM_SWITCH_GROUP, grim.GRIM_SWITCH_WARP, 0):
+            grim.grim_index_set_shape(idx, read_range_kb=1024, read_switch=switch, all_bins_path=path)
+            assert_same(gpu_filter(idx, rs), want)
+    idx.close()
+
+
 def test_default_coarse_factor_q5():
     from paper_1708_04329_gb300 import synth
 
