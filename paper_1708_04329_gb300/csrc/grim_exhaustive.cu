@@ -42,6 +42,12 @@
 //   it runs on the FMA pipe instead.
 // * Early exit: after each 16-token block the group stops a read once every
 //   one of its 1024 bins is dead -- exact, since a dead bin can never pass.
+//   With the warp switch and 1024-bin tiles the test is one warp vote per
+//   block: the warp takes new reads once every lane has no live bin or is
+//   past its read's last block.  A group that ended reads on through its
+//   token row's padding (the tokeniser fills each row to its stride with
+//   the never-miss token), so its counters hold; a per-lane count of the
+//   blocks that left a live bin gives each read's useful blocks.
 // * Groups stay converged: the per-block work is the same instruction stream
 //   for all groups of a warp, and every warp collective uses the full mask.
 //   Taking a next read (new counters, the claim, the prefetch of the read
@@ -353,6 +359,7 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
     // WS, 1024-bin tiles: blocks since the warp's last switch, and the word
     // kept in the one-word tail
     uint32_t bk = 0, kt = 0;
+    uint32_t alive = 0;  // WS, 1024-bin tiles: blocks after which this lane had a live bin
     bool fin = false;
     Counters<P> c;
     c.init(0);
@@ -423,64 +430,10 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
     bool active = __any_sync(0xFFFFFFFFu, !fin);
     bool waiting = false;  // WS: the group's read has ended; it waits for the warp's switch
 
-    // (2) one 16-token block for all groups, to NW words per lane: from the
-    //     slot, or for the blocks past the slot's rows (long reads at q = 6)
-    //     from L2; (3) then the end-of-read test.  True when the warp took
-    //     new reads.
-    auto run_block = [&](auto words) -> bool {
+    // the passing bins of the groups whose reads ended (emit), then new
+    // reads for them (done); the warp runs this together
+    auto emit_and_switch = [&](bool done, bool emit, auto words) {
       constexpr int NW = decltype(words)::value;
-      {
-        uint4 t0, t1;
-        const uint32_t bi = nblk - left;  // this read's block index
-        // (1024-bin tiles: whole reads in slots; waiting groups read padding)
-        if (TW == 32 || fin || waiting || bi < a.slot_blocks) {
-          t0 = lds128(tp);
-          t1 = lds128(tp + 16u);
-        } else {
-          const uint4* g = reinterpret_cast<const uint4*>(
-              a.rv.tokens + ((uint64_t)cur * a.rv.copies + copy) * a.rv.ts + bi * kBlockTokens);
-          t0 = __ldg(g);
-          t1 = __ldg(g + 1);
-        }
-        const uint32_t tw[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-        if constexpr (NW == 1) add_block<P, 1>(c, tw, lane_base + kt * 4u, a);
-        else add_block<P, 4>(c, tw, lane_base, a);
-      }
-      tp += step;
-      --left;
-
-      // a read ends when every bin of its tile is dead or its tokens are
-      // used up; one ballot per block, the rest only when some group ends
-      const uint32_t all_dead = c.dead[0] & c.dead[1] & c.dead[2] & c.dead[3];
-      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, all_dead == ~0u);
-      const bool gdead = (bal & gmask) == gmask;
-      bool done = !fin && !waiting && (gdead || left == 0);
-      if (WS && done) {
-        // freeze the group's counters (padding adds no misses) until every
-        // group of the warp has ended its read
-        executed += nblk - left;
-        if (NW == 1) tail_exec += nblk - left;
-        waiting = true;
-        tp = pad_tokens;
-        step = 0;
-      }
-      bool take_next;
-      if constexpr (!WS) {
-        take_next = __any_sync(0xFFFFFFFFu, done);
-      } else if constexpr (TW == 32) {
-        take_next = __all_sync(0xFFFFFFFFu, fin || waiting);
-      } else {
-        // sixteen groups: switch once enough of them wait, so that a few
-        // long reads do not hold the rest (the others keep their reads)
-        take_next = __popc(__ballot_sync(0xFFFFFFFFu, fin || waiting)) >= a.switch_lanes;
-      }
-      if (!take_next) return false;
-      if (WS) {
-        done = waiting;
-      } else if (done) {
-        executed += nblk - left;
-      }
-      const bool emit = done && !gdead;
       if (__any_sync(0xFFFFFFFFu, emit)) {
         // in the one-word tail slot 0 holds word kt and slots 1..3 are dead
         uint32_t pm[4], cnt = 0;
@@ -521,6 +474,93 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
       switch_reads(done);
       waiting = false;
       active = __any_sync(0xFFFFFFFFu, !fin);
+    };
+
+    // (2) one 16-token block for all groups, to NW words per lane: from the
+    //     slot, or for the blocks past the slot's rows (long reads at q = 6)
+    //     from L2; (3) then the end-of-read test.  True when the warp took
+    //     new reads.
+    auto run_block = [&](auto words) -> bool {
+      constexpr int NW = decltype(words)::value;
+      {
+        uint4 t0, t1;
+        const uint32_t bi = nblk - left;  // this read's block index
+        // (1024-bin tiles: whole reads in slots; waiting groups read padding)
+        if (TW == 32 || fin || waiting || bi < a.slot_blocks) {
+          t0 = lds128(tp);
+          t1 = lds128(tp + 16u);
+        } else {
+          const uint4* g = reinterpret_cast<const uint4*>(
+              a.rv.tokens + ((uint64_t)cur * a.rv.copies + copy) * a.rv.ts + bi * kBlockTokens);
+          t0 = __ldg(g);
+          t1 = __ldg(g + 1);
+        }
+        const uint32_t tw[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
+        if constexpr (NW == 1) add_block<P, 1>(c, tw, lane_base + kt * 4u, a);
+        else add_block<P, 4>(c, tw, lane_base, a);
+      }
+      tp += step;
+      --left;
+
+      // a read ends when every bin of its tile is dead or its tokens are
+      // used up
+      const uint32_t all_dead = c.dead[0] & c.dead[1] & c.dead[2] & c.dead[3];
+      if constexpr (WS && TW == 32) {
+        // lockstep: one vote per block.  The warp takes new reads once every
+        // lane has no live bin or is past its read's last block (a group
+        // without a read has left = ~0).  A group whose read ended reads on
+        // through its token row's padding (never a miss), so its counters
+        // keep their values; a dead group may apply its remaining tokens
+        // (dead bins stay dead).
+        const bool ldead = all_dead == ~0u;
+        alive += ldead ? 0u : 1u;
+        if (!__all_sync(0xFFFFFFFFu, ldead || (int)left <= 0)) return false;
+        const bool gdead = (__ballot_sync(0xFFFFFFFFu, ldead) & gmask) == gmask;
+        // blocks the read needed: up to the one after which its last live
+        // lane died, or all of them
+        uint32_t m = alive;
+        m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, 1));
+        m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, 2));
+        m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, 4));
+        const uint32_t used = min(nblk, m + 1u);
+        const bool done = !fin;
+        if (done) {
+          executed += used;
+          if (NW == 1 && used > kTailAfter) tail_exec += used - kTailAfter;
+        }
+        alive = 0;
+        emit_and_switch(done, done && !gdead, Words<NW>{});
+        return true;
+      }
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, all_dead == ~0u);
+      const bool gdead = (bal & gmask) == gmask;
+      bool done = !fin && !waiting && (gdead || left == 0);
+      if (WS && done) {
+        // freeze the group's counters (padding adds no misses) until every
+        // group of the warp has ended its read
+        executed += nblk - left;
+        if (NW == 1) tail_exec += nblk - left;
+        waiting = true;
+        tp = pad_tokens;
+        step = 0;
+      }
+      bool take_next;
+      if constexpr (!WS) {
+        take_next = __any_sync(0xFFFFFFFFu, done);
+      } else if constexpr (TW == 32) {
+        take_next = __all_sync(0xFFFFFFFFu, fin || waiting);
+      } else {
+        // sixteen groups: switch once enough of them wait, so that a few
+        // long reads do not hold the rest (the others keep their reads)
+        take_next = __popc(__ballot_sync(0xFFFFFFFFu, fin || waiting)) >= a.switch_lanes;
+      }
+      if (!take_next) return false;
+      if (WS) {
+        done = waiting;
+      } else if (done) {
+        executed += nblk - left;
+      }
+      emit_and_switch(done, done && !gdead, Words<NW>{});
       return true;
     };
 
@@ -546,9 +586,6 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
         if (__all_sync(0xFFFFFFFFu, (lm & (lm - 1u)) == 0u)) {
           kt = lm ? (uint32_t)__ffs(lm) - 1u : 0u;
           c.keep_one(kt, lm != 0u);
-          // tail blocks of a read = its blocks when it ends - the first four
-          // (the subtraction wraps until the addition at its end)
-          if (!fin && !waiting) tail_exec -= kTailAfter;
           while (!run_block(Words<1>{})) {
           }
           bk = 0;
