@@ -195,7 +195,22 @@ def test_reads_of_every_length_in_one_call():
     rs = Reads(reads, [int(x) for x in rng.integers(0, 6, len(reads))])
     idx = build(g, 64, 5, 255)
     oix = oracle.bin_vectors(g, 64, 5, 255)
-    assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
+    want = oracle.filter(oix, rs)
+    assert_same(gpu_filter(idx, rs), want)
+    # and with every read switch and both all-bins paths forced: under the
+    # warp switch the groups of a warp end 1 to 16 blocks apart, so groups
+    # whose read ended read on through their token rows' padding
+    from paper_1708_04329_gb300 import grim
+
+    for path in (grim.GRIM_PATH_TWO_LEVEL, grim.GRIM_PATH_EXACT):
+        for switch in (grim.GRIM_SWITCH_GROUP, grim.GRIM_SWITCH_WARP):
+            grim.grim_index_set_shape(idx, read_switch=switch, all_bins_path=path)
+            assert_same(gpu_filter(idx, rs), want)
+    # reversed length order: long and short reads share every warp
+    back = Reads(reads[::-1], list(rs.e[::-1]))
+    grim.grim_index_set_shape(idx, read_switch=grim.GRIM_SWITCH_WARP)
+    assert_same(gpu_filter(idx, back), oracle.filter(oix, back))
+    idx.close()
 
 
 def test_zero_reads():
