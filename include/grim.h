@@ -138,11 +138,13 @@ int grim_build_host(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint3
 
 /* The all-bins path (grim_shape).  Automatic (0): coarse-then-exact when the
  * index has the coarse and bin-major tables and its super-bin window would
- * hold at most 40% of the 4^q tokens in a uniform random sequence (denser
- * coarse tables let too many super-bins pass: at q = 5, B = 200 that is
- * reads up to about 200 bp), else one exact pass; a batch whose tightest
- * read has fewer than 24 tokens of slack takes the exact pass too.  An
- * index with only one of the two paths' tables always takes that path. */
+ * hold at most 50% of the 4^q tokens in a uniform random sequence (denser
+ * coarse tables let too many super-bins pass: at q = 5, B = 200 that is an
+ * index for reads up to about 300 bp), else one exact pass; a batch whose
+ * tightest read has fewer than 24 tokens of slack takes the exact pass too,
+ * and so does a call whose coarse survivors exceed its record room (320 a
+ * read, or the output capacity if larger).  An index with only one of the
+ * two paths' tables always takes that path. */
 #define GRIM_PATH_TWO_LEVEL 1u /* coarse pass over super-bins, then exact checks */
 #define GRIM_PATH_EXACT 2u     /* one exact pass over every bin                  */
 
@@ -150,8 +152,8 @@ int grim_build_host(const char* ref, uint64_t len, uint32_t B, uint32_t q, uint3
 typedef struct {
   /* bins per super-bin of the coarse table (1..64).  0 chooses the largest
    * power of two up to 64 whose super-bin window (f*B + ext bases) would
-   * hold at most 40% of all 4^q tokens in a uniform random sequence: 2 at
-   * q = 5, B = 200, ext = 99 and 16 at q = 6, B = 100, ext = 149.  Larger
+   * hold at most 50% of all 4^q tokens in a uniform random sequence: 2 at
+   * q = 5, B = 200, ext = 99 or 249 and 16 at q = 6, B = 100, ext = 149.  Larger
    * factors shrink the coarse pass but let more super-bins pass it; the best
    * value depends on the genome too (the package's autotuner measures it). */
   uint32_t coarse_factor;
@@ -200,9 +202,11 @@ int grim_index_info(const grim_index* idx, grim_index_desc* out);
  *                  ended early idle until every group's read has ended, and
  *                  then switches all of them at once (fewer switches, some
  *                  idle blocks).  Automatic: WARP when every read of the
- *                  batch spans the same number of 16-token blocks (so no
- *                  group idles for long), GROUP otherwise; graph plans, whose
- *                  batches are not known when they are captured, use GROUP
+ *                  batch spans the same number of 16-token blocks and has
+ *                  the same miss budget D' (so reads leave a tile at similar
+ *                  blocks and no group idles for long), GROUP otherwise;
+ *                  graph plans, whose batches are not known when they are
+ *                  captured, use GROUP
  *   all_bins_path  GRIM_PATH_TWO_LEVEL, GRIM_PATH_EXACT, or 0 (automatic; see
  *                  GRIM_PATH_*)
  * Results do not depend on the shape.  Graph plans take the shape when they
@@ -340,7 +344,7 @@ int grim_filter_host(const grim_index* idx, const char* reads, const uint64_t* o
  *     max_read_len - q + 1 rounded up to a multiple of 16 (196 bytes for an
  *     index built for 100 bp reads at q = 5, 484 bytes for 250 bp), times 4
  *     for the token copies of the all-bins mode at q = 6; then 18 bytes per
- *     record of capacity, which is cap, or max(cap, 64 * n_reads) for an
+ *     record of capacity, which is cap, or max(cap, 320 * n_reads) for an
  *     index with the coarse layout (room for the coarse pass's survivors),
  *     whose records take another 4 * coarse_factor bytes each for the
  *     survivors' expanded candidate lists.
@@ -585,6 +589,13 @@ typedef struct {
                                   warp read switch: the last blocks of a read once every
                                   lane of the warp has at most one 32-bin word with a live
                                   bin) tests 256 of the tile's bins                       */
+  uint32_t read_switch;        /* all-bins mode: GRIM_SWITCH_GROUP or GRIM_SWITCH_WARP, as
+                                  chosen for the call (automatic: WARP when every read
+                                  spans as many 16-token blocks and has the same miss
+                                  budget D' = min(q*e, L-q+1)); 0 in candidate mode      */
+  uint32_t all_bins_path;      /* all-bins mode: GRIM_PATH_TWO_LEVEL or GRIM_PATH_EXACT,
+                                  the path the call took (after any fallback); 0 in
+                                  candidate mode                                          */
 } grim_filter_stats;
 
 /* Counters of the calling thread's last successful grim_filter /

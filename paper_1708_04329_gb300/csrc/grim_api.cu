@@ -28,10 +28,14 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 // Default bins per super-bin: the largest power of two (2..64) whose
-// super-bin window of f*B + ext bases would hold at most 40% of the 4^q
+// super-bin window of f*B + ext bases would hold at most 50% of the 4^q
 // tokens if the sequence were uniform random (1 - exp(-q-grams / 4^q)); a
 // denser coarse table lets too many super-bins pass.  q = 5, B = 200,
-// ext = 99 gives 2; q = 6, B = 100, ext = 149 gives 16.
+// ext = 99 or 249 gives 2 (38% and 47%); q = 6, B = 100, ext = 149 gives 16.
+// The same bound decides whether the coarse pass is taken automatically:
+// measured on GB300, f = 2 with ext = 249 (47%) beat one exact pass by 39%
+// on 100-250 bp reads once its survivors had room, and f = 4 with ext = 99
+// (58%) lost to f = 2 by 2.4x.
 // Fraction of the 4^q tokens a super-bin window of f bins (f*B + ext bases)
 // would hold in a uniform random sequence.
 double coarse_density(uint32_t B, uint32_t q, uint32_t ext, uint32_t f) {
@@ -39,7 +43,7 @@ double coarse_density(uint32_t B, uint32_t q, uint32_t ext, uint32_t f) {
   const double grams = (double)f * B + ext - q + 1;
   return 1.0 - exp(-grams / tokens);
 }
-constexpr double kCoarseDensityMax = 0.40;
+constexpr double kCoarseDensityMax = 0.50;
 
 uint32_t default_coarse_factor(uint32_t B, uint32_t q, uint32_t ext) {
   uint32_t best = 2;
@@ -524,6 +528,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   ReadsView rv{tokens, meta, n_reads, token_stride(v), copies};
   const uint32_t bin_bits = v.num_bins > 1 ? bit_length(v.num_bins - 1) : 0;
   uint64_t survivors = 0;
+  uint32_t switch_used = 0, path_used = 0;  // all-bins mode: what the call took
   const uint32_t read_bits = n_reads > 1 ? bit_length((uint64_t)n_reads - 1) : 0;
 
   CK(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
@@ -558,11 +563,15 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
     bool forced = false;
     bool two = all_bins_path(idx, &forced) == kPathCoarse && (forced || min_slack >= 24);
     // automatic read switch: a warp's lane groups take their next reads
-    // together when every read has as many 16-token blocks (no group waits
-    // long for the others), each on its own otherwise
+    // together when every read has as many 16-token blocks and the same miss
+    // budget D' (reads then leave a tile at similar blocks, so no group
+    // waits long for the others), each on its own otherwise
     ExhShape shape = idx->shape;
     if (!shape.read_switch)
-      shape.read_switch = h.blk_max + h.blk_lo == 32u ? GRIM_SWITCH_WARP : GRIM_SWITCH_GROUP;
+      shape.read_switch = h.blk_max + h.blk_lo == 32u && h.max_d + h.d_lo == 255u
+                              ? GRIM_SWITCH_WARP
+                              : GRIM_SWITCH_GROUP;
+    switch_used = shape.read_switch;
     if (two) {
       const IndexView& cv = idx->cv;
       const uint32_t cbits = cv.num_bins > 1 ? bit_length(cv.num_bins - 1) : 0;
@@ -594,6 +603,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
       // restart the record and work counters for the next pass
       CK(cudaMemsetAsync(ctl, 0, offsetof(Ctl, blocks), st));
     }
+    path_used = two ? GRIM_PATH_TWO_LEVEL : GRIM_PATH_EXACT;
     if (two) launch_candidates(v, rv, lists, lists_off, ra, ctl, st, "candidates_refine");
     else launch_exhaustive(v, rv, ra, bin_bits, h.max_d, ctl, st, "exhaustive", {false, 0},
                            shape);
@@ -622,6 +632,8 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
       (h.blocks - h.tail_blocks) * kBlockTokens * exhaustive_tile_bins(v.r4) +
       h.tail_blocks * kBlockTokens * (exhaustive_tile_bins(v.r4) / 4);
   g_last_stats.survivors = survivors;
+  g_last_stats.read_switch = switch_used;
+  g_last_stats.all_bins_path = path_used;
   return GRIM_OK;
 }
 

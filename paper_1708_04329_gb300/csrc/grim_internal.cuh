@@ -38,7 +38,8 @@ struct Ctl {
   uint32_t blk_max;                // most 16-token blocks of a read in the batch
   uint32_t blk_lo;                 // 32 - the fewest 16-token blocks of a read
   unsigned long long tail_blocks;  // of `blocks`: applied to one word per lane (256 bins)
-  uint32_t pad[42];
+  uint32_t d_lo;                   // 255 - the smallest miss budget D' of the batch
+  uint32_t pad[41];
 };
 static_assert(sizeof(Ctl) == 256, "Ctl is one 256-byte slot");
 static_assert(offsetof(Ctl, live_reads) == 32, "live counts follow the per-pass counters");
@@ -225,8 +226,12 @@ struct Layout {
 };
 
 // Survivors of the coarse pass get their own capacity: reads from repeat
-// families survive in many super-bins that then fail the exact check.
-constexpr uint64_t kSurvivorsPerRead = 64;
+// families survive in many super-bins that then fail the exact check.  On
+// the 3.1 Gbp synthetic genome: 27 a read for 100 bp reads with e = 5 and
+// ext = 99; against an index with ext = 249, 132 for the serving mix of
+// 100-250 bp reads and 263 for 100 bp reads with e uniform in 0..5.  A call
+// whose survivors do not fit takes the exact pass.
+constexpr uint64_t kSurvivorsPerRead = 320;
 
 inline uint64_t record_capacity(uint32_t n_reads, uint64_t cap, uint32_t coarse_factor) {
   const uint64_t s = coarse_factor ? kSurvivorsPerRead * n_reads : 0;

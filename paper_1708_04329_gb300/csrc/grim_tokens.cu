@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(kTokWarps * 32) k_tokenise(
     meta[r] = ntok | (d << 8);
     // most batches share one budget: skip the atomics once the max is reached
     if (d > *reinterpret_cast<volatile uint32_t*>(&ctl->max_d)) atomicMax(&ctl->max_d, d);
+    if (255u - d > *reinterpret_cast<volatile uint32_t*>(&ctl->d_lo)) atomicMax(&ctl->d_lo, 255u - d);
     const uint32_t tight = 255u - (ntok - d);
     if (tight > *reinterpret_cast<volatile uint32_t*>(&ctl->max_tight))
       atomicMax(&ctl->max_tight, tight);

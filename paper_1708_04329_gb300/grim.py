@@ -87,7 +87,8 @@ class _Desc(C.Structure):
 class _Stats(C.Structure):
     _fields_ = [("n_reads", C.c_uint64), ("n_records", C.c_uint64), ("pairs", C.c_uint64),
                 ("tokens_executed", C.c_uint64), ("survivors", C.c_uint64),
-                ("bit_tests_executed", C.c_uint64)]
+                ("bit_tests_executed", C.c_uint64), ("read_switch", C.c_uint32),
+                ("all_bins_path", C.c_uint32)]
 
 
 class _BuildOpts(C.Structure):

@@ -68,8 +68,8 @@ def test_every_launch_shape_matches_oracle(world):
         d = idx.desc
         assert (d.cta_threads, d.read_range_kb, d.read_switch, d.all_bins_path) == (640, 48 << 10, 0, 0)
         # reads up to 250 bp: super-bins of 2 x 200 bp hold ~47% of all tokens,
-        # so the automatic path is the exact pass
-        assert d.two_level == 0
+        # under the 50% bound, so the automatic path is coarse-then-exact
+        assert d.two_level == (layouts == grim.GRIM_LAYOUT_ALL)
         for bad in ((600, 0, 0), (0, 512, 0), (0, (4 << 20) + 1, 0), (0, 0, 3), (0, 0, 0, 3)):
             with pytest.raises(grim.GrimError) as ei:
                 grim.grim_index_set_shape(idx, *bad)

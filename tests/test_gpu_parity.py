@@ -520,3 +520,35 @@ def test_one_word_tail(path):
     assert_same(got[grim.GRIM_SWITCH_WARP], want)
     assert_same(got[grim.GRIM_SWITCH_GROUP], want)
     idx.close()
+
+
+def test_automatic_read_switch_and_path():
+    """The choices a call makes on its own, reported by grim_last_filter_stats:
+    the warp switch only when every read spans as many 16-token blocks and
+    has the same miss budget D' (with budgets that differ, reads leave a tile
+    blocks apart); coarse-then-exact unless a read has too little slack.  The
+    pass list equals the oracle's in every case."""
+    from paper_1708_04329_gb300 import grim, synth
+
+    g = synth.human_genome(1_000_000, seed=97)
+    idx = build(g, 200, 5, 150)
+    oix = oracle.bin_vectors(g, 200, 5, 150)
+    W, G = grim.GRIM_SWITCH_WARP, grim.GRIM_SWITCH_GROUP
+    two, exact = grim.GRIM_PATH_TWO_LEVEL, grim.GRIM_PATH_EXACT
+    cases = [
+        (synth.reads(g, 1500, seed=98, lengths=(100,), e=5, max_edits=5), W, two),
+        (synth.reads(g, 1500, seed=99, lengths=(100,), e_frac=(5, 100), max_edits=None), G, two),
+        (synth.reads(g, 1500, seed=100, lengths=(100, 150), probs=(0.5, 0.5), e=5, max_edits=5), G, two),
+        # 96 tokens, D' = 75: slack 21 < 24, so the exact pass
+        (synth.reads(g, 600, seed=101, lengths=(100,), e=15, max_edits=3), W, exact),
+    ]
+    for rs, switch, path in cases:
+        assert_same(gpu_filter(idx, rs), oracle.filter(oix, rs))
+        st = grim.grim_last_filter_stats()
+        assert (st["read_switch"], st["all_bins_path"]) == (switch, path)
+    # candidate mode reports neither
+    off, cand = synth.candidates((cases[0][0].true_pos // 200).astype(np.int32), oix.num_bins, seed=3)
+    gpu_filter(idx, cases[0][0], off, cand)
+    st = grim.grim_last_filter_stats()
+    assert (st["read_switch"], st["all_bins_path"]) == (0, 0)
+    idx.close()
