@@ -977,6 +977,7 @@ def _serve_trace(srv, rs, trace, paced: bool, max_outstanding: int = 1 << 17,
     lat, reads_done, merged = [], [0], []
     wait, run, breads = [], [], []
     outstanding = [0]
+    errors = []
     cv = threading.Condition()
 
     def collect():
@@ -985,7 +986,13 @@ def _serve_trace(srv, rs, trace, paced: bool, max_outstanding: int = 1 << 17,
             if item is None:
                 return
             ticket, target, n = item
-            (r, _b, _c), info = srv.result(ticket)
+            try:
+                (r, _b, _c), info = srv.result(ticket)
+            except BaseException as ex:  # stop the submitter too; it re-raises
+                errors.append(ex)
+                with cv:
+                    cv.notify_all()
+                return
             lat.append(info.t_done_ns - target)
             merged.append(info.batch_requests)
             wait.append(info.t_launch_ns - info.t_submit_ns)
@@ -996,32 +1003,41 @@ def _serve_trace(srv, rs, trace, paced: bool, max_outstanding: int = 1 << 17,
                 outstanding[0] -= n
                 cv.notify()
 
-    th = threading.Thread(target=collect)
+    th = threading.Thread(target=collect, daemon=True)
     th.start()
     t0 = time.monotonic_ns()
     lag = []
-    for i in range(len(trace["t"])):
-        n = int(trace["size"][i])
-        if paced:
-            target = t0 + int(trace["t"][i] * 1e9)
-            now = time.monotonic_ns()
-            if target > now:
-                time.sleep((target - now) / 1e9)
-        else:
+    try:
+        for i in range(len(trace["t"])):
+            n = int(trace["size"][i])
+            if paced:
+                target = t0 + int(trace["t"][i] * 1e9)
+                now = time.monotonic_ns()
+                if target > now:
+                    time.sleep((target - now) / 1e9)
+            else:
+                with cv:
+                    cv.wait_for(lambda: errors or outstanding[0] + n <= max_outstanding
+                                or outstanding[0] == 0)
+                target = time.monotonic_ns()
+            if errors:
+                break
+            req = _request(rs, int(trace["start"][i]), n)
+            t_sub = time.monotonic_ns()
+            lag.append(t_sub - target)
             with cv:
-                cv.wait_for(lambda: outstanding[0] + n <= max_outstanding or outstanding[0] == 0)
-            target = time.monotonic_ns()
-        req = _request(rs, int(trace["start"][i]), n)
-        t_sub = time.monotonic_ns()
-        lag.append(t_sub - target)
-        with cv:
-            outstanding[0] += n
-        q.put((srv.submit(**req), target, n))
-        if (time.monotonic_ns() - t0) / 1e9 > time_limit_s:
-            break
-    t_last = time.monotonic_ns()
-    q.put(None)
-    th.join()
+                outstanding[0] += n
+            q.put((srv.submit(**req), target, n))
+            if (time.monotonic_ns() - t0) / 1e9 > time_limit_s:
+                break
+    finally:
+        # the collector always gets its end mark, so a failed submit cannot
+        # leave it waiting
+        t_last = time.monotonic_ns()
+        q.put(None)
+        th.join()
+    if errors:
+        raise errors[0]
     t_end = time.monotonic_ns()
     lat_ms = np.array(lat) / 1e6
     return {"requests": len(lat), "reads": reads_done[0], "elapsed_s": (t_end - t0) / 1e9,
@@ -1143,6 +1159,9 @@ def run_serve(args, rank, world, local):
 
     from paper_1708_04329_gb300 import grim, synth
 
+    if args.serve_slot_reads < 8192 and not 0 < args.serve_chunk <= args.serve_slot_reads:
+        raise SystemExit("requests reach 8192 reads: slots of fewer reads need "
+                         "--serve-chunk between 1 and --serve-slot-reads")
     torch.cuda.set_device(local)
     t0 = time.perf_counter()
     w = synth.serving(n=args.genome)
