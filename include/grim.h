@@ -272,6 +272,8 @@ int grim_trim_scratch(void);
 /*
  * Bytes of device workspace grim_filter needs for n_reads reads, n_cand
  * candidates (0 in all-bins mode) and an output capacity of cap records.
+ * All-bins mode on an index with the coarse table also holds room for the
+ * coarse pass's survivors (320 records a read); candidate mode does not.
  */
 uint64_t grim_filter_workspace_size(const grim_index* idx, uint32_t n_reads, uint64_t n_cand,
                                     uint64_t cap);

@@ -484,9 +484,11 @@ void grim_free(grim_index* idx) {
 uint64_t grim_filter_workspace_size(const grim_index* idx, uint32_t n_reads, uint64_t n_cand,
                                     uint64_t cap) {
   if (!idx) return 0;
-  // all-bins mode needs at least as much as candidate mode
-  return layout(idx->v, n_reads, cap, two_level_capable(idx) ? idx->factor : 0,
-                token_copies(idx->v, n_cand > 0))
+  // room for coarse survivors only in all-bins mode (n_cand == 0); a
+  // candidate-mode call with no candidates gets the larger all-bins figure
+  const bool all_bins = n_cand == 0;
+  return layout(idx->v, n_reads, cap, all_bins && two_level_capable(idx) ? idx->factor : 0,
+                token_copies(idx->v, !all_bins))
       .total;
 }
 
@@ -508,7 +510,7 @@ int grim_filter(const grim_index* idx, const char* reads, const uint64_t* offset
   if (cap && (!out_read || !out_bin || !out_count)) return GRIM_E_ARG;
   if (cap > 0xFFFFFFFFull) return GRIM_E_ARG;
   const IndexView& v = idx->v;
-  const uint32_t f = capable ? idx->factor : 0;
+  const uint32_t f = capable && !cand_mode ? idx->factor : 0;  // survivors: all-bins mode
   const uint32_t copies = token_copies(v, cand_mode);
   const Layout L = layout(v, n_reads, cap, f, copies);
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) return GRIM_E_ARG;
