@@ -51,12 +51,12 @@ UNIT = "reads/s"
 TRAFFIC = {
     # all-bins kernel, 1M reads of 100 bp (4 read ranges), linear in the
     # tiles swept: captures at 0.4 and 0.8 Gbp (977 and 1,954 coarse tiles:
-    # 1.276 and 2.125 GB per launch) give 0.427 GB + 0.869 MB per tile;
+    # 1.291 and 2.158 GB per launch) give 0.424 GB + 0.887 MB per tile;
     # 7,569 coarse tiles of the 3.1 Gbp table
-    ("6fa51ad40cd45d87", "human:exhaustive_coarse"): 7_002_752_024,
+    ("7fb9beabe0ae85ab", "human:exhaustive_coarse"): 7_139_935_662,
     # the same rule for the one exact pass over bins (1,954 and 3,907 tiles:
-    # 1.984 and 3.426 GB; 0.541 GB + 0.738 MB per tile); 15,137 tiles
-    ("6fa51ad40cd45d87", "human:exhaustive_exact"): 11_719_408_896,
+    # 2.008 and 3.600 GB; 0.415 GB + 0.815 MB per tile); 15,137 tiles
+    ("7fb9beabe0ae85ab", "human:exhaustive_exact"): 12_753_206_628,
     # candidate kernel, in proportion to the pairs gathered: the 3.1 Gbp
     # bin-major table (1.98 GB, as at full size) with 100k ragged reads,
     # 32,876,582 pairs, 4.314 GB (131.2 B per pair); 1,320,234,389 pairs
