@@ -22,8 +22,8 @@
 // * Each group copies the token row of the read it will take next into its
 //   own shared-memory slot with cp.async while it works on the current one,
 //   so the inner loop does not wait on global memory.  At TW = 8 a slot
-//   holds only a read's first block (more warps fit beside the tile) and
-//   later blocks are loaded from L2.
+//   holds a read's first blocks (up to four, as many as fit beside the tile
+//   at the CTA size) and later blocks are loaded from L2.
 // * Reads are swept in ranges whose token rows fit in L2, range by range,
 //   so concurrent CTAs on different tiles share the same token rows.
 // * Instead of p separate counters, each lane keeps bit-sliced vertical
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
     switch_reads(true);
     const uint32_t gmask = kGroupMask << (grp * GL);
     bool active = __any_sync(0xFFFFFFFFu, !fin);
-    bool waiting = false;  // WS: the group's read has ended; it waits for the warp's switch
+    bool waiting = false;  // WS, 256-bin tiles: the group's read has ended; it waits for a switch
 
     // the passing bins of the groups whose reads ended (emit), then new
     // reads for them (done); the warp runs this together
@@ -536,8 +536,8 @@ __global__ void __launch_bounds__(NT, 1) k_exhaustive(ExhArgs a) {
       const bool gdead = (bal & gmask) == gmask;
       bool done = !fin && !waiting && (gdead || left == 0);
       if (WS && done) {
-        // freeze the group's counters (padding adds no misses) until every
-        // group of the warp has ended its read
+        // freeze the group's counters (padding adds no misses) until the
+        // warp switches
         executed += nblk - left;
         if (NW == 1) tail_exec += nblk - left;
         waiting = true;
