@@ -51,12 +51,12 @@ UNIT = "reads/s"
 TRAFFIC = {
     # all-bins kernel, 1M reads of 100 bp (4 read ranges), linear in the
     # tiles swept: captures at 0.4 and 0.8 Gbp (977 and 1,954 coarse tiles:
-    # 1.291 and 2.158 GB per launch) give 0.424 GB + 0.887 MB per tile;
+    # 1.292 and 2.174 GB per launch) give 0.409 GB + 0.903 MB per tile;
     # 7,569 coarse tiles of the 3.1 Gbp table
-    ("7fb9beabe0ae85ab", "human:exhaustive_coarse"): 7_139_935_662,
+    ("164bfabfb98b2648", "human:exhaustive_coarse"): 7_245_892_095,
     # the same rule for the one exact pass over bins (1,954 and 3,907 tiles:
-    # 2.008 and 3.600 GB; 0.415 GB + 0.815 MB per tile); 15,137 tiles
-    ("7fb9beabe0ae85ab", "human:exhaustive_exact"): 12_753_206_628,
+    # 1.995 and 3.578 GB; 0.411 GB + 0.811 MB per tile); 15,137 tiles
+    ("164bfabfb98b2648", "human:exhaustive_exact"): 12_680_709_263,
     # candidate kernel, in proportion to the pairs gathered: the 3.1 Gbp
     # bin-major table (1.98 GB, as at full size) with 100k ragged reads,
     # 32,876,582 pairs, 4.314 GB (131.2 B per pair); 1,320,234,389 pairs
