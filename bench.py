@@ -57,6 +57,11 @@ TRAFFIC = {
     # the same rule for the one exact pass over bins (1,954 and 3,907 tiles:
     # 1.995 and 3.578 GB; 0.411 GB + 0.811 MB per tile); 15,137 tiles
     ("164bfabfb98b2648", "human:exhaustive_exact"): 12_680_709_263,
+    # the all-bins kernel at q = 6 (finer index, 1M reads of 150 bp, 27 read
+    # ranges), linear in the 256-bin coarse tiles: captures at 0.4 and 0.6 Gbp
+    # (977 and 1,465 tiles: 5.736 and 7.452 GB per launch) give 2.301 GB +
+    # 3.516 MB per tile; 7,569 tiles of the 3.1 Gbp coarse table
+    ("164bfabfb98b2648", "finer:exhaustive_coarse"): 28_913_063_934,
     # candidate kernel, in proportion to the pairs gathered: the 3.1 Gbp
     # bin-major table (1.98 GB, as at full size) with 100k ragged reads,
     # 32,876,582 pairs, 4.314 GB (131.2 B per pair); 1,320,234,389 pairs
