@@ -552,3 +552,38 @@ def test_automatic_read_switch_and_path():
     st = grim.grim_last_filter_stats()
     assert (st["read_switch"], st["all_bins_path"]) == (0, 0)
     idx.close()
+
+
+def test_survivor_overflow_takes_the_exact_pass():
+    """Coarse survivors beyond their room (the larger of the output capacity
+    and 320 a read) with the token-major table present: the call drops the
+    coarse result and takes the exact pass, reports that path, and still
+    equals the oracle.  The genome repeats one random 127-base period: a
+    super-bin window (2 x 24 + 79 = 127 bases) holds nearly every q-gram of
+    the period, so ~998 super-bins pass per read, while a bin window (103
+    bases) holds a read's q-grams only near its copies (~551 bins a read)."""
+    from paper_1708_04329_gb300 import grim
+
+    rng = np.random.default_rng(41)
+    period = "".join("ACGT"[i] for i in rng.integers(0, 4, 127))
+    ref = (period * (48_000 // 127 + 1))[:48_000]
+    reads = []
+    for _ in range(20):
+        s = int(rng.integers(0, len(ref) - 80))
+        reads.append(ref[s:s + 80])
+    rs = Reads(reads, [1] * len(reads))
+    g = _np(ref)
+    want = oracle.filter(oracle.bin_vectors(g, 24, 5, 80), rs)
+    n_surv = len(oracle.filter(oracle.bin_vectors(g, 48, 5, 80), rs)[0])
+    assert n_surv > max(len(want[0]), 320 * rs.n)  # the survivors do not fit
+    idx = build(g, 24, 5, 80, coarse_factor=2)
+    grim.grim_index_set_shape(idx, all_bins_path=grim.GRIM_PATH_TWO_LEVEL)
+    assert_same(gpu_filter(idx, rs, cap=len(want[0])), want)
+    st = grim.grim_last_filter_stats()
+    assert st["survivors"] == n_surv
+    assert st["all_bins_path"] == grim.GRIM_PATH_EXACT
+    # with room for every survivor the same call stays on the coarse path
+    assert_same(gpu_filter(idx, rs, cap=n_surv), want)
+    st = grim.grim_last_filter_stats()
+    assert st["survivors"] == n_surv and st["all_bins_path"] == grim.GRIM_PATH_TWO_LEVEL
+    idx.close()
