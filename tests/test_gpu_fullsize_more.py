@@ -6,6 +6,8 @@ workloads, in the launch configurations the benchmark times.
   read against every bin (coarse-then-exact), and candidate lists.
 * Ragged candidates: 4,000,000 reads of L in {100,150,250} with per-read e
   and 1.32e9 candidates, through one graph-captured plan launch.
+* Serving index: the same genome with max_read_len 250, its automatic
+  coarse-then-exact path on reads of the serving pool.
 
 The oracle checks what it can compute exactly (every bin for sampled reads,
 every read for a bin range, the lists of the first reads) and properties
@@ -121,4 +123,34 @@ def test_ragged_full_size_plan():
     assert (np.diff(r.astype(np.int64)) >= 0).all()
     true_key = np.arange(rs.n, dtype=np.uint64) << np.uint64(32) | (rs.true_pos // w["B"]).astype(np.uint64)
     assert np.isin(true_key, key).all()
+    idx.close()
+
+
+def test_serving_index_two_level_at_full_size():
+    """The serving index at full size: the 3.1 Gbp genome with B=200, q=5
+    and max_read_len 250 (ext = 249, super-bin windows ~47% full), whose
+    automatic all-bins path is coarse-then-exact.  50,000 reads of the
+    serving pool (100-250 bp, e up to 5% of L): every bin for 24 sampled
+    reads equals the oracle, and the exact pass gives the same pass list
+    record for record."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_04329_gb300 import grim, synth
+
+    w = synth.serving()
+    rs = w["reads"].subset(np.arange(50_000))
+    idx = build(w["genome"], w["B"], w["q"], w["max_read_len"])
+    assert idx.desc.two_level == 1
+    got = gpu_filter(idx, rs, cap=64 * rs.n)
+    st = grim.grim_last_filter_stats()
+    assert st["all_bins_path"] == grim.GRIM_PATH_TWO_LEVEL
+    assert st["read_switch"] == grim.GRIM_SWITCH_GROUP  # mixed lengths and budgets
+    oix = oracle.bin_vectors(w["genome"], w["B"], w["q"], w["max_read_len"])
+    sample = np.linspace(0, rs.n - 1, 24).astype(np.int64)
+    _check_slices(got, *oracle.filter(oix, rs.subset(sample)), sample)
+    grim.grim_index_set_shape(idx, all_bins_path=grim.GRIM_PATH_EXACT)
+    exact = gpu_filter(idx, rs, cap=64 * rs.n)
+    assert grim.grim_last_filter_stats()["all_bins_path"] == grim.GRIM_PATH_EXACT
+    for a, b in zip(exact, got):
+        assert np.array_equal(a, b)
     idx.close()
